@@ -1,0 +1,473 @@
+#!/usr/bin/env python
+"""Throughput of the CKKS homomorphic linear transformation on one GB300.
+
+Workload (one "step" = one LT, the whole hot path): N = 2^16 ring, one
+ciphertext at the top level (24 Q limbs: 55b + 23x40b), 4 special 60-bit
+primes, dnum 6 (alpha 4, beta 6), a 2^15 x 2^15 matrix with 256 consecutive
+nonzero diagonals, evaluated by triple-hoisted BSGS (Algorithm 2) with the
+library's split.  Keys, diagonals and the ciphertext are uniform residues
+drawn on the device (the work does not depend on the values); the keys and
+the diagonals (6+ GB) stay resident and are far larger than L2, so no flush
+is needed between steps.
+
+Prints one JSON line (rank 0):
+  value      LT/s over all ranks with inputs resident in HBM (device events)
+  e2e        LT/s through the C ABI with the ciphertext copied from pinned
+             host memory and the result copied back inside each step
+  roofline   the dominant kernel's algorithmic bytes / its live event-timed
+             duration, against the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle timed on this host on one LT of the workload
+
+--impl reference times the CPU oracle alone (the reference arm).
+Multi-GPU: under torchrun each rank runs its own replica of the workload
+(independent LTs; no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted LT/s and ms per LT at N=2^16 (bit-exact), % of HBM roofline; p50/p99"
+PARAMS = "n16"
+D = 256
+LEVEL = 24
+SEED = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="th", choices=["th", "dh", "bsgs", "diag"])
+    ap.add_argument("--split", default="", help="e.g. 4,8,8 (default: the library's choice)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--diags", type=int, default=256, help="number of diagonals (256 = the benchmark workload)")
+    ap.add_argument("--level", type=int, default=24, help="ciphertext level (24 = the benchmark workload)")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def shard(total: int, world: int, rank: int) -> range:
+    """Units of work of one rank when `total` independent units are split."""
+    per, extra = divmod(total, world)
+    start = rank * per + min(rank, extra)
+    return range(start, start + per + (1 if rank < extra else 0))
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- byte model
+def algorithmic_bytes(cls: str, split, level: int, k: int, beta: int, n_diag: int, N: int) -> tuple:
+    """(bytes, launches) per LT of one kernel class in the TH/DH schedule:
+    the words the step must read and write once (keys, diagonals, digits,
+    inputs, outputs), 8 bytes each."""
+    n1, n2, n3 = split
+    ext = level + k
+    limb = 8 * N
+    if cls == "diag_mac":
+        limbs = n_diag * ext                                   # diagonals
+        limbs += (n2 - 1) * 2 * beta * ext                      # middle-layer keys
+        limbs += (n1 * beta * ext) if n2 > 1 else 0             # digits of each baby index
+        limbs += 2 * (n1 - 1) * ext + 2 * level                 # baby pairs (A_i, B_i) and the input ciphertext
+        limbs += 2 * n3 * ext                                   # outputs u_k
+        return limbs * limb, 1
+    if cls == "ks_inner":
+        p1 = (n1 - 1) * (beta * ext + 2 * beta * ext + level + 2 * ext)
+        p5 = (n3 - 1) * (beta * ext + 2 * beta * ext + ext + 4 * ext)
+        return (p1 + p5) * limb, (n1 - 1) + (n3 - 1)
+    return None, None
+
+
+def lt_compulsory_bytes(split, level: int, k: int, beta: int, n_diag: int, N: int) -> int:
+    """Compulsory bytes of one LT: diagonals, distinct keys, ciphertext in and out."""
+    n1, n2, n3 = split
+    keys = (n1 - 1) + (n2 - 1) + (n3 - 1)
+    ext = level + k
+    return 8 * N * (n_diag * ext + keys * 2 * beta * ext + 2 * level + 2 * (level - 1))
+
+
+def source_digest(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def ncu_traffic(cls: str):
+    """dram bytes per launch of `cls` from the committed ncu summary, or None
+    when the kernel's sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(cls)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    if rec.get("source_digest") != source_digest(rec.get("sources", [])):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_problem_from_device(ps, g, split, keys_t, diags_t, ct_t):
+    import numpy as np
+    from paper_2605_17222_gb300 import binding
+    keys = {r: binding.to_host(t).reshape(g.beta_max, 2, ps.L + ps.k, ps.n) for r, t in keys_t.items()}
+    diags = binding.to_host(diags_t)
+    ct = binding.to_host(ct_t)
+    return keys, np.ascontiguousarray(diags), (np.ascontiguousarray(ct[0]), np.ascontiguousarray(ct[1]))
+
+
+def time_oracle(ps, algo, split, keys, diags, ct, budget_s: float, max_steps: int):
+    """Times full oracle LTs until `max_steps` or `budget_s` (at least one)."""
+    from oracle import lt as olt
+    from oracle.ckks import Ctx
+    octx = Ctx(ps)
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max(1, max_steps):
+        t0 = time.perf_counter()
+        olt.run(octx, algo, ct, diags, keys, split if algo != "diag" else None)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start + times[-1] > budget_s:
+            break
+    return times
+
+
+def cores_used() -> int:
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
+
+
+# ----------------------------------------------------------------------------- main arms
+def make_inputs(g, ps, split, algo, device):
+    import torch
+    from paper_2605_17222_gb300 import synth
+    N = ps.n
+    rots = g.required_rotations(algo, split if algo != "diag" else None, D, 1)
+    keys_t = {}
+    for r in rots:
+        t = synth.uniform_mod_device(SEED, f"key/{r}", ps.moduli, N, count=2 * g.beta_max, device=device)
+        g.upload_rotation_key_device(r, t)
+        keys_t[r] = t
+    top = list(ps.q) + list(ps.p)
+    diags_t = synth.uniform_mod_device(SEED, "diag", top, N, count=D, device=device)
+    f = g.upload_diagonals_device(diags_t, stride=1, level=ps.L)
+    ct_t = synth.uniform_mod_device(SEED, "ct", list(ps.q[:LEVEL]), N, count=2, device=device)
+    torch.cuda.synchronize()
+    return rots, keys_t, diags_t, f, ct_t
+
+
+def run_ours(args, dist: Dist):
+    global D, LEVEL
+    D, LEVEL = args.diags, args.level
+    import numpy as np
+    import torch
+    from paper_2605_17222_gb300 import binding, synth
+    device = f"cuda:{dist.local}"
+    torch.cuda.set_device(dist.local)
+    ps = synth.param_set(PARAMS)
+    g = binding.Context.from_params(ps, device=dist.local)
+    algo = args.algo
+    if args.split:
+        split = tuple(int(x) for x in args.split.split(","))
+    else:
+        split = g.choose_split(algo, LEVEL, D)
+    split3 = tuple(split) + (1,) * (3 - len(split))
+    rots, keys_t, diags_t, f, ct_t = make_inputs(g, ps, split3, algo, device)
+    ct = g.ct_wrap(ct_t, LEVEL)
+    out = g.ct_empty(LEVEL - 1)
+    keep_host_copy = not args.no_cpu_baseline and dist.rank == 0 and dist.world == 1
+    if not keep_host_copy:  # the library holds its own copies
+        keys_t, diags_t = None, None
+        torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    beta = g.beta(LEVEL)
+
+    # warm-up; the first warm-up steps also rank the kernel classes by device time
+    for c in binding.KERNEL_CLASSES:
+        binding.profile_enable(c, True)
+    binding.profile_reset()
+    for _ in range(max(3, args.warmup)):
+        g.lt_eval(ct, f, algo, split3, out=out)
+    torch.cuda.synchronize()
+    shares = {c: binding.profile_read(c) for c in binding.KERNEL_CLASSES}
+    for c in binding.KERNEL_CLASSES:
+        binding.profile_enable(c, False)
+    tot = sum(v[0] for v in shares.values()) or 1.0
+    dominant = max(shares, key=lambda c: shares[c][0])
+    if algo in ("th", "dh") and dominant not in ("diag_mac", "ks_inner"):
+        # the roofline below is defined for the HBM-streaming kernels
+        dominant = max(("diag_mac", "ks_inner"), key=lambda c: shares[c][0])
+
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    time.sleep(0.3)
+    # ---------------------------------------------------------------- timed: device-resident inputs
+    binding.profile_reset()
+    binding.profile_enable(dominant, True)
+    l0 = binding.kernel_launches()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        g.lt_eval(ct, f, algo, split3, out=out)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    launches = binding.kernel_launches() - l0
+    dom_ms, dom_n = binding.profile_read(dominant)
+    binding.profile_enable(dominant, False)
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    # ---------------------------------------------------------------- timed: end to end through the C ABI
+    e2e = None
+    if not args.no_e2e:
+        n_in, n_out = 2 * LEVEL * ps.n, 2 * (LEVEL - 1) * ps.n
+        h_in = torch.empty(n_in, dtype=torch.int64, pin_memory=True)
+        h_in.copy_(ct_t.reshape(-1).cpu())
+        h_out = torch.empty(n_out, dtype=torch.int64, pin_memory=True)
+        hin = h_in.numpy().view(np.uint64)
+        hout = h_out.numpy().view(np.uint64)
+        d_in = g.ct_create(LEVEL)
+        d_out = g.ct_create(LEVEL - 1)
+        for _ in range(2):
+            g.h2d_async(d_in, hin)
+            g.lt_eval(d_in, f, algo, split3, out=d_out)
+            g.d2h_async(d_out, hout)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_steps = max(1, args.steps // 2)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            g.h2d_async(d_in, hin)
+            g.lt_eval(d_in, f, algo, split3, out=d_out)
+            g.d2h_async(d_out, hout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        e2e_ms = dist.max(e0.elapsed_time(e1))
+        e2e = {"value": round(dist.world * e2e_steps / (e2e_ms / 1e3), 3), "unit": "LT/s",
+               "h2d_bytes_per_step": n_in * 8, "d2h_bytes_per_step": n_out * 8,
+               "ms_per_step": round(e2e_ms / e2e_steps, 4)}
+    clk = clocks.stop()
+
+    max_ms = dist.max(total_ms)
+    value = dist.world * args.steps / (max_ms / 1e3)
+    srt = sorted(step_ms)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(round(0.99 * (len(srt) - 1))))]
+    # ---------------------------------------------------------------- roofline of the dominant kernel
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    b_lt, n_lt = algorithmic_bytes(dominant, split3, LEVEL, ps.k, beta, D, ps.n)
+    roof = None
+    if b_lt and dom_n:
+        per_launch = b_lt / n_lt
+        avg_s = dom_ms / dom_n / 1e3
+        ach = per_launch / avg_s / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": ncu_traffic(dominant),
+                "algorithmic_bytes_per_launch": int(per_launch), "avg_launch_ms": round(avg_s * 1e3, 4),
+                "peak_source": f"{peak_src} HBM copy bandwidth"}
+    lt_bytes = lt_compulsory_bytes(split3, LEVEL, ps.k, beta, D, ps.n) if algo in ("th", "dh") else None
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "LT/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4),
+        "p50_ms": round(p50, 4), "p99_ms": round(p99, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (uniform residues drawn on the device; seeded)",
+        "config": {"workload": f"single LT: N=2^16, level {LEVEL} (Q = 55b + 23x40b), 4x60b special primes, "
+                               f"dnum 6, {D} consecutive diagonals, one ciphertext at the top level",
+                   "algo": algo, "split": list(split3), "parallelism": f"replicas x{dist.world}",
+                   "l2": "inputs larger than L2 (keys + diagonals resident, > 6 GB per step); no flush"},
+        "hbm_roofline_lt": (None if lt_bytes is None else {
+            "compulsory_bytes": lt_bytes, "achieved_gbs": round(lt_bytes / (max_ms / args.steps / 1e3) / 1e9, 1),
+            "frac": round(lt_bytes / (max_ms / args.steps / 1e3) / 1e9 / peak, 4)}),
+        "roofline": roof,
+        "kernel_shares": {c: round(v[0] / tot, 4) for c, v in shares.items()},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    # ---------------------------------------------------------------- CPU oracle baseline
+    if not args.no_cpu_baseline and dist.rank == 0 and dist.world == 1:
+        keys, diags, cth = oracle_problem_from_device(ps, g, split3, keys_t, diags_t, ct_t)
+        times = time_oracle(ps, algo, split3, keys, diags, cth, budget_s=30.0, max_steps=1)
+        result["cpu_baseline"] = {
+            "value": round(len(times) / sum(times), 5), "unit": "LT/s", "cores": cores_used(), "kind": "oracle",
+            "sample": f"{len(times)} full LT(s) of this workload ({algo}, split {list(split3)}) on the same "
+                      f"uniform inputs copied to the host; {sum(times):.1f} s"}
+    return result
+
+
+def run_reference(args, dist: Dist):
+    """The CPU oracle as the reference arm, on this host's cores."""
+    global D, LEVEL
+    D, LEVEL = args.diags, args.level
+    if dist.rank != 0:
+        return None
+    import numpy as np
+    from paper_2605_17222_gb300 import synth
+    ps = synth.param_set(PARAMS)
+    split = tuple(int(x) for x in args.split.split(",")) if args.split else (4, 8, 8)
+    split3 = tuple(split) + (1,) * (3 - len(split))
+    N = ps.n
+    alpha = -(-ps.L // ps.dnum)
+    beta_max = -(-ps.L // alpha)
+    top = list(ps.q) + list(ps.p)
+    from oracle import lt as olt
+    rots = olt.rotation_set(args.algo, D, split3 if args.algo != "diag" else None, 1, N // 2)
+    keys = {r: synth.uniform_mod(SEED, f"key/{r}", top * (2 * beta_max), N).reshape(beta_max, 2, len(top), N)
+            for r in rots}
+    diags = np.stack([synth.uniform_mod(SEED, f"diag/{t}", top, N) for t in range(D)])
+    ct = (synth.uniform_mod(SEED, "ct0", ps.q[:LEVEL], N), synth.uniform_mod(SEED, "ct1", ps.q[:LEVEL], N))
+    # warm-up: one small LT of the same algorithm (the oracle has no state to warm beyond its threads)
+    budget = 150.0
+    times = time_oracle(ps, args.algo, split3, keys, diags, ct, budget_s=budget, max_steps=args.steps)
+    total = sum(times)
+    v = len(times) / total
+    return {
+        "metric": METRIC, "value": round(v, 5), "unit": "LT/s", "n_gpus": dist.world, "steps": len(times),
+        "warmup": 0, "ms_per_step": round(1e3 * total / len(times), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic (uniform residues, seeded)",
+        "config": {"workload": f"single LT: N=2^16, level {LEVEL}, 4x60b special primes, dnum 6, {D} consecutive "
+                               f"diagonals", "algo": args.algo, "split": list(split3), "parallelism": "cpu"},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(v, 5), "unit": "LT/s", "cores": cores_used(), "kind": "oracle",
+                         "sample": f"{len(times)} full oracle LT(s) of the workload (time budget {budget:.0f} s "
+                                   f"caps the {args.steps} requested steps; no warm-up: the oracle keeps no state)"},
+        "e2e": {"value": round(v, 5), "unit": "LT/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            res = run_reference(args, dist)
+        else:
+            res = run_ours(args, dist)
+        if dist.rank == 0 and res is not None:
+            print(json.dumps(res), flush=True)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

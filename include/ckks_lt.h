@@ -1,0 +1,234 @@
+/*
+ * ckks_lt.h - C ABI of the GB300 library for the CKKS homomorphic linear
+ * transformation (plaintext matrix times encrypted slot vector).
+ *
+ * Paper: S. Akherati, X. Zhang, "Triple-Hoisted Baby-Step Giant-Step Linear
+ * Transformation over CKKS Homomorphic Encryption and Hardware Accelerator".
+ * The calls follow the paper's problem statement: an RNS-CKKS context
+ * (Sec. II-A; parameter sets as in Table "HE parameters": N, L+1, alpha, beta),
+ * rotation (Galois) keys, a ciphertext, the encoded diagonals of the matrix
+ * and their offsets, and the LT algorithm: diagonal method (Sec. II-B),
+ * BSGS (Eq. 5), double-hoisted BSGS (Algorithm 1) or triple-hoisted BSGS
+ * (Algorithm 2, Eq. 6).
+ *
+ * Data conventions (every call):
+ *   - A "limb" is N uint64 words holding residues modulo one prime, canonical
+ *     in [0, q).  A polynomial is consecutive limbs.
+ *   - Ring elements are in the NTT domain, bit-reversed order: word s of a
+ *     limb holds a(psi^(2*brv(s)+1)), psi the primitive 2N-th root of unity
+ *     x^((q-1)/2N) for the smallest integer x >= 2 with psi^N = -1 (mod q).
+ *   - The context's moduli are q_0..q_{L-1} (the Q chain) then p_0..p_{k-1}
+ *     (special primes, P = prod p_i).  Every modulus must be prime, = 1 mod 2N,
+ *     below 2^60, and all must be distinct.
+ *   - A ciphertext at level l has l Q limbs: layout [2][l][N] (c0 then c1).
+ *   - An "extended" polynomial at level l has l + k limbs: q_0..q_{l-1} then
+ *     p_0..p_{k-1}.
+ *   - alpha = ceil(L / dnum) limbs per digit; at level l there are
+ *     beta_l = ceil(l / alpha) digits, digit b holding Q limbs
+ *     [alpha*b, min(alpha*(b+1), l)).
+ *   - Rotation by r slots is to the left: new slot j = old slot j + r, through
+ *     the automorphism x -> x^(5^r mod 2N) (Eq. 2).
+ *
+ * Ownership: the library copies host buffers into device memory it owns;
+ * handles are freed with the matching ckks_free_* call and all of them by
+ * ckks_ctx_destroy.  Buffers passed as device pointers stay owned by the
+ * caller and must outlive every call that uses them.
+ *
+ * Errors: every call returns a ckks_status; nothing is thrown across the ABI.
+ * ckks_last_error() gives a message for the calling thread.  Validation
+ * failures return before any device work is queued.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls that take a stream are asynchronous on it unless stated.
+ * Device scratch memory is taken from the stream-ordered allocator of the
+ * context's device and returned on the same stream.
+ */
+#ifndef CKKS_LT_H
+#define CKKS_LT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ckks_ctx ckks_ctx;
+typedef struct ckks_ct ckks_ct;
+typedef struct ckks_diags ckks_diags;
+
+typedef enum {
+    CKKS_OK = 0,
+    CKKS_EINVAL = 1,   /* bad argument, shape, level or split            */
+    CKKS_ENOMEM = 2,   /* device or host allocation failed               */
+    CKKS_ENOKEY = 3,   /* a rotation key the algorithm needs is missing  */
+    CKKS_ECUDA = 4,    /* a CUDA runtime call failed                     */
+    CKKS_ETIMEOUT = 5, /* a bounded device-side wait gave up             */
+    CKKS_EBUSY = 6     /* resource in use                                */
+} ckks_status;
+
+typedef enum {
+    LT_DIAG = 0,     /* diagonal method, hoisted (Sec. II-B)             */
+    LT_BSGS = 1,     /* baby-step giant-step (Eq. 5)                     */
+    LT_DH_BSGS = 2,  /* double-hoisted BSGS (Algorithm 1)                */
+    LT_TH_BSGS = 3   /* triple-hoisted BSGS (Algorithm 2)                */
+} lt_algo;
+
+/* Baby/giant split: TH uses (n'1, n'2, n'3) with n1*n2*n3 = D; BSGS and DH
+ * use (n1, n2) with n3 = 1 and n1*n2 = D; the diagonal method ignores it.
+ * All zero (or a NULL pointer) asks the library to choose. */
+typedef struct {
+    uint32_t n1, n2, n3;
+} lt_split;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device` for ring degree N = 2^log_n
+ * (10 <= log_n <= 17), Q chain q[0..n_q-1], special primes p[0..n_p-1]
+ * (n_p >= 1) and dnum digits at the top level (Sec. II-A, Fig. 1).
+ * Computes and uploads every constant (twiddles, basis-conversion tables).
+ * EINVAL on a modulus that is not an NTT-friendly prime below 2^60. */
+ckks_status ckks_ctx_create(ckks_ctx** out, uint32_t log_n, const uint64_t* q, uint32_t n_q,
+                            const uint64_t* p, uint32_t n_p, uint32_t dnum, int device);
+ckks_status ckks_ctx_destroy(ckks_ctx* ctx);
+
+/* Upload the switching key from phi_r(s) to s for left rotation by r slots,
+ * in standard (un-hoisted) form (Fig. 1).  Host layout [beta_max][2][L+k][N]
+ * (beta_max = ceil(L/alpha); all L Q limbs then all k P limbs), n_words must
+ * equal beta_max*2*(L+k)*N.  The same key serves every algorithm and split:
+ * the hoisted form swk~_r = phi_{-r}(swk_r) of Algorithms 1-2 is applied as
+ * an index gather on the digits.  r is taken mod N/2; replacing a key is
+ * allowed when no queued work uses it. */
+ckks_status ckks_upload_rotation_key(ckks_ctx* ctx, int32_t r, const uint64_t* host, size_t n_words);
+/* Same, from a device buffer the library copies (stream-ordered). */
+ckks_status ckks_upload_rotation_key_device(ckks_ctx* ctx, int32_t r, const uint64_t* dev,
+                                            size_t n_words, void* stream);
+int ckks_has_rotation_key(const ckks_ctx* ctx, int32_t r);
+
+/* Upload the encoded, un-rotated diagonals f_t (t < n_diag) of the matrix,
+ * with offsets o_t = offset0 + stride*t (Sec. II-B: f_t packs diagonal o_t).
+ * Host layout [n_diag][level + k][N]: Q limbs q_0..q_{level-1} then the k P
+ * limbs, NTT domain.  `level` is the level the diagonals were encoded at; an
+ * LT at a ciphertext level l <= level uses the first l Q limbs and the P
+ * limbs.  offset0 must be 0 (EINVAL otherwise). */
+ckks_status ckks_upload_diagonals(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t offset0,
+                                  int32_t stride, uint32_t level, const uint64_t* host, size_t n_words);
+/* Same, from a device buffer the library copies (stream-ordered on `stream`). */
+ckks_status ckks_upload_diagonals_device(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t offset0,
+                                         int32_t stride, uint32_t level, const uint64_t* dev, size_t n_words,
+                                         void* stream);
+ckks_status ckks_free_diags(ckks_diags* f);
+
+/* ------------------------------------------------------------------ ciphertexts */
+
+/* New device ciphertext at `level` (library-owned, contents undefined). */
+ckks_status ckks_ct_create(ckks_ctx* ctx, ckks_ct** out, uint32_t level);
+/* New device ciphertext holding a copy of host [2][level][N] (synchronous). */
+ckks_status ckks_ct_upload(ckks_ctx* ctx, ckks_ct** out, uint32_t level, const uint64_t* host);
+/* Wrap caller-owned device memory [2][level][N] (e.g. a torch tensor). */
+ckks_status ckks_ct_wrap_device(ckks_ctx* ctx, ckks_ct** out, uint32_t level, uint64_t* dev_ptr);
+/* Stream-ordered copies between a ciphertext and host memory (pinned host
+ * memory makes them asynchronous; n_words must be 2*level*N). */
+ckks_status ckks_ct_h2d_async(ckks_ct* ct, const uint64_t* host, size_t n_words, void* stream);
+ckks_status ckks_ct_d2h_async(const ckks_ct* ct, uint64_t* host, size_t n_words, void* stream);
+/* Synchronous download (waits for the whole device). */
+ckks_status ckks_ct_download(const ckks_ct* ct, uint64_t* host, size_t n_words);
+uint32_t ckks_ct_level(const ckks_ct* ct);
+uint64_t* ckks_ct_device_ptr(const ckks_ct* ct);
+ckks_status ckks_free_ct(ckks_ct* ct);
+
+/* ------------------------------------------------------------------ the LT */
+
+/* out <- LT_F(in): the diagonals f applied to `in` by algorithm `algo` with
+ * `split` (NULL or all-zero = the library's choice, written to `chosen` if it
+ * is not NULL).  `out` must have level in->level - 1: the hoisted algorithms
+ * end with ModDown merged with rescale (Algorithm 2 line 19), BSGS with the
+ * rescale of Eq. (1).  Rotation amounts are multiples of f's stride; ENOKEY
+ * when a needed key is missing.  in->level must be >= 2 and <= f's level.
+ * Asynchronous on `stream`. */
+ckks_status lt_eval(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_algo algo,
+                    const lt_split* split, ckks_ct* out, void* stream, lt_split* chosen);
+
+/* `count` independent LTs, possibly at different levels and with different
+ * diagonal sets, queued as one unit on `stream`: LTs that share a diagonal
+ * set and level are evaluated together so that every key and diagonal limb is
+ * read from HBM once per group.  algos may be NULL (TH-BSGS for all);
+ * splits may be NULL (library choice).  Results equal count separate
+ * lt_eval calls bit for bit when the same splits are used. */
+ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* in,
+                          const ckks_diags* const* f, const lt_algo* algos, const lt_split* splits,
+                          ckks_ct* const* out, void* stream);
+
+/* Rotation amounts (mod N/2, ascending, multiples of stride) whose keys the
+ * algorithm needs for n_diag diagonals and this split; returns how many were
+ * written (at most cap), or -1 on a bad split. */
+int32_t lt_required_rotations(const ckks_ctx* ctx, lt_algo algo, const lt_split* split,
+                              uint32_t n_diag, int32_t stride, int32_t* rot_out, uint32_t cap);
+
+/* The split the library would choose for (algo, level, n_diag). */
+ckks_status lt_choose_split(ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out);
+
+/* ------------------------------------------------------------------ steps
+ * The steps of the key-switching path (Fig. 1), each on caller-owned device
+ * buffers, asynchronous on `stream`.  They are what lt_eval is built from
+ * and are exported for step-by-step checking and custom schedules. */
+
+/* Forward (inverse = 0) or inverse (inverse = 1) negacyclic NTT, in place, of
+ * a polynomial at `level` with (ext = 1) or without (ext = 0) the P limbs. */
+ckks_status ckks_poly_ntt(ckks_ctx* ctx, uint64_t* poly, uint32_t level, int ext, int inverse, void* stream);
+
+/* Decompose (ModUp), Fig. 1 and Eq. (3): digits of phi_rot(c) (rot = 0: of c)
+ * over the extended basis.  c: [level][N]; digits: [beta_level][level+k][N]. */
+ckks_status ckks_decompose(ckks_ctx* ctx, uint32_t level, const uint64_t* c, int32_t rot,
+                           uint64_t* digits, void* stream);
+
+/* Switching-key inner product with hoisted automorphism (Alg. 2 lines 4-5):
+ *   out0 = phi_rot(x0 + <d, swk~_0>),  out1 = phi_rot(<d, swk~_1>)
+ * with swk~ = phi_{-rot}(swk_key_rot), evaluated as phi_rot(x0) + <phi_rot(d), swk>.
+ * digits [beta_level][level+k][N]; x0 NULL (zero), an extended polynomial
+ * [level+k][N] (lift_x0 = 0) or a Q-only polynomial [level][N] lifted to
+ * P*x0 (lift_x0 = 1, Alg. 2 line 2).  accumulate = 1 adds the result to
+ * out0/out1 instead of overwriting them (Alg. 2 lines 17-18). */
+ckks_status ckks_ks_inner(ckks_ctx* ctx, uint32_t level, const uint64_t* digits, int32_t key_rot,
+                          int32_t rot, const uint64_t* x0, int lift_x0, uint64_t* out0, uint64_t* out1,
+                          int accumulate, void* stream);
+
+/* ModDown, Eq. (4): x [level+k][N] -> out [level][N]. */
+ckks_status ckks_moddown(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out, void* stream);
+
+/* ModDown merged with rescale (Alg. 2 line 19): x [level+k][N] ->
+ * out [level-1][N], dividing by P * q_{level-1} (Eq. 4 over the basis
+ * {q_{level-1}, p_0..p_{k-1}}). */
+ckks_status ckks_moddown_rescale(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out,
+                                 void* stream);
+
+/* Rescale, Eq. (1): x [level][N] -> out [level-1][N]. */
+ckks_status ckks_rescale(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out, void* stream);
+
+/* Automorphism phi_rot in the NTT domain (Eq. 7) of n_limbs limbs that hold
+ * any moduli (a pure index gather): out[s] = in[src(s)]. */
+ckks_status ckks_automorphism(ckks_ctx* ctx, uint32_t n_limbs, const uint64_t* in, int32_t rot,
+                              uint64_t* out, void* stream);
+
+/* ------------------------------------------------------------------ misc */
+const char* ckks_last_error(void);
+size_t ckks_device_bytes_in_use(const ckks_ctx* ctx);
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t ckks_kernel_launch_count(void);
+
+/* Live per-kernel timing.  Kernel classes: "diag_mac" (plaintext-diagonal
+ * multiply-accumulate with the fused middle key-switch layer), "ks_inner"
+ * (switching-key inner product), "ntt_fwd_cols", "ntt_fwd_rows",
+ * "ntt_inv_rows", "ntt_inv_cols" (the two passes of the forward and inverse
+ * NTT), "automorphism", "add_gather".  While a class is enabled every launch
+ * of it is bracketed by CUDA events on its own stream.  ckks_profile_read
+ * waits for the recorded events and returns the summed device time (ms) and
+ * the number of launches since the last reset.  EINVAL on an unknown name. */
+ckks_status ckks_profile_enable(const char* kernel_class, int on);
+ckks_status ckks_profile_read(const char* kernel_class, double* total_ms, uint64_t* launches);
+void ckks_profile_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CKKS_LT_H */

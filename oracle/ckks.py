@@ -215,11 +215,13 @@ class Ctx:
         return self.ntt(self.residues(self.encode_coeffs(z, scale), basis), basis)
 
     def crt_centered(self, res: np.ndarray, basis) -> np.ndarray:
-        """Centered integer from the first two limbs (|m| < q0 q1 / 4 asserted)."""
-        q0, q1 = basis[0], basis[1]
-        inv = pow(q0, -1, q1)
+        """Centered integer from the first two limbs, or the only limb
+        (|m| < modulus / 4 asserted)."""
+        q0 = basis[0]
+        q1 = basis[1] if len(basis) > 1 else 1
+        inv = pow(q0, -1, q1) if q1 > 1 else 0
         r0 = [int(v) for v in res[0]]
-        r1 = [int(v) for v in res[1]]
+        r1 = [int(v) for v in res[1]] if q1 > 1 else [0] * self.N
         M = q0 * q1
         out = np.empty(self.N, dtype=object)
         for i in range(self.N):

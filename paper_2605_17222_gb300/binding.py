@@ -1,0 +1,381 @@
+"""Python binding of the C ABI in include/ckks_lt.h (ctypes; argument
+marshalling only).  Device memory for ciphertexts and step buffers is held in
+torch tensors (int64 storage, read as uint64 residues by the library) and the
+stream is torch's current CUDA stream unless one is given.  Every step runs in
+the library's CUDA kernels; there is no CPU path: if the library cannot be
+built or loaded, or there is no GPU, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+LT_DIAG, LT_BSGS, LT_DH_BSGS, LT_TH_BSGS = 0, 1, 2, 3
+ALGOS = {"diag": LT_DIAG, "bsgs": LT_BSGS, "dh": LT_DH_BSGS, "th": LT_TH_BSGS}
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ckks_lt.h")
+
+
+class CkksError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ckks status {status}: {msg}")
+        self.status = status
+
+
+class Split(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_uint32), ("n2", ctypes.c_uint32), ("n3", ctypes.c_uint32)]
+
+    def tuple(self):
+        return (self.n1, self.n2, self.n3)
+
+
+_lib = None
+
+
+def declared_functions() -> list:
+    """Names of the functions include/ckks_lt.h declares."""
+    with open(HEADER) as f:
+        text = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n.startswith(("ckks_", "lt_"))))
+
+
+def lib():
+    """Load the library, building it first if the sources are newer."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    P, U32, I32, SZ, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_size_t, ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "ckks_ctx_create": [PP, U32, P, U32, P, U32, U32, I],
+        "ckks_ctx_destroy": [P],
+        "ckks_upload_rotation_key": [P, I32, P, SZ],
+        "ckks_upload_rotation_key_device": [P, I32, P, SZ, P],
+        "ckks_upload_diagonals": [P, PP, U32, I32, I32, U32, P, SZ],
+        "ckks_upload_diagonals_device": [P, PP, U32, I32, I32, U32, P, SZ, P],
+        "ckks_free_diags": [P],
+        "ckks_ct_create": [P, PP, U32],
+        "ckks_ct_upload": [P, PP, U32, P],
+        "ckks_ct_wrap_device": [P, PP, U32, P],
+        "ckks_ct_h2d_async": [P, P, SZ, P],
+        "ckks_ct_d2h_async": [P, P, SZ, P],
+        "ckks_ct_download": [P, P, SZ],
+        "ckks_free_ct": [P],
+        "lt_eval": [P, P, P, I, P, P, P, P],
+        "lt_eval_batch": [P, U32, P, P, P, P, P, P],
+        "lt_choose_split": [P, I, U32, U32, P],
+        "ckks_poly_ntt": [P, P, U32, I, I, P],
+        "ckks_decompose": [P, U32, P, I32, P, P],
+        "ckks_ks_inner": [P, U32, P, I32, I32, P, I, P, P, I, P],
+        "ckks_moddown": [P, U32, P, P, P],
+        "ckks_moddown_rescale": [P, U32, P, P, P],
+        "ckks_rescale": [P, U32, P, P, P],
+        "ckks_automorphism": [P, U32, P, I32, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.ckks_last_error.restype = ctypes.c_char_p
+    L.ckks_device_bytes_in_use.argtypes = [P]
+    L.ckks_device_bytes_in_use.restype = SZ
+    L.ckks_kernel_launch_count.restype = ctypes.c_uint64
+    L.ckks_has_rotation_key.argtypes = [P, I32]
+    L.ckks_has_rotation_key.restype = I
+    L.lt_required_rotations.argtypes = [P, I, P, U32, I32, P, U32]
+    L.lt_required_rotations.restype = I32
+    L.ckks_ct_level.argtypes = [P]
+    L.ckks_ct_level.restype = U32
+    L.ckks_ct_device_ptr.argtypes = [P]
+    L.ckks_ct_device_ptr.restype = P
+    _lib = L
+    return L
+
+
+def check(st: int) -> None:
+    if st != 0:
+        raise CkksError(st, lib().ckks_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("the CKKS LT library needs a CUDA GPU")
+    return torch
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, np.ndarray):
+        assert t.dtype == np.uint64 and t.flags.c_contiguous
+        return ctypes.c_void_p(t.ctypes.data)
+    assert t.is_contiguous() and t.is_cuda and t.element_size() == 8
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def to_device(a: np.ndarray, device=None):
+    """Host uint64 array -> device int64 tensor with the same bits."""
+    torch = _torch()
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64))
+    return t.to(device or "cuda", non_blocking=False)
+
+
+def to_host(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+@dataclass
+class Ciphertext:
+    handle: ctypes.c_void_p
+    level: int
+    tensor: object  # backing torch tensor [2][level][N] (None if library-owned)
+    ctx: "Context"
+
+    def numpy(self) -> np.ndarray:
+        if self.tensor is not None:
+            _torch().cuda.synchronize()
+            return to_host(self.tensor)
+        out = np.empty((2, self.level, self.ctx.N), dtype=np.uint64)
+        check(lib().ckks_ct_download(self.handle, _ptr(out), out.size))
+        return out
+
+    def free(self):
+        if self.handle:
+            check(lib().ckks_free_ct(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.ckks_free_ct(self.handle)
+        except Exception:
+            pass
+
+
+class Diagonals:
+    def __init__(self, ctx, handle, n_diag, stride, level):
+        self.ctx, self.handle, self.n_diag, self.stride, self.level = ctx, handle, n_diag, stride, level
+
+    def free(self):
+        if self.handle:
+            check(lib().ckks_free_diags(self.handle))
+            self.handle = None
+
+
+class Context:
+    """An RNS-CKKS context on one GPU (ckks_ctx_create)."""
+
+    def __init__(self, log_n: int, q, p, dnum: int, device: int = 0):
+        _torch()
+        L = lib()
+        self.log_n, self.N = log_n, 1 << log_n
+        self.q, self.p = [int(v) for v in q], [int(v) for v in p]
+        self.L, self.k, self.dnum = len(self.q), len(self.p), dnum
+        self.alpha = -(-self.L // dnum)
+        self.beta_max = -(-self.L // self.alpha)
+        self.device = device
+        qa = np.array(self.q, dtype=np.uint64)
+        pa = np.array(self.p, dtype=np.uint64)
+        h = ctypes.c_void_p()
+        check(L.ckks_ctx_create(ctypes.byref(h), log_n, _ptr(qa), len(qa), _ptr(pa), len(pa), dnum, device))
+        self.h = h
+
+    @classmethod
+    def from_params(cls, ps, device: int = 0):
+        return cls(ps.log_n, ps.q, ps.p, ps.dnum, device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(lib().ckks_ctx_destroy(self.h))
+            self.h = None
+
+    def beta(self, level: int) -> int:
+        return -(-level // self.alpha)
+
+    def bytes_in_use(self) -> int:
+        return lib().ckks_device_bytes_in_use(self.h)
+
+    # ----------------------------------------------------------- keys / diagonals
+    def upload_rotation_key(self, r: int, key: np.ndarray) -> None:
+        key = np.ascontiguousarray(key, dtype=np.uint64)
+        check(lib().ckks_upload_rotation_key(self.h, int(r), _ptr(key), key.size))
+
+    def upload_rotation_key_device(self, r: int, key_t, stream=None) -> None:
+        check(lib().ckks_upload_rotation_key_device(self.h, int(r), _ptr(key_t), key_t.numel(), _stream(stream)))
+
+    def has_key(self, r: int) -> bool:
+        return bool(lib().ckks_has_rotation_key(self.h, int(r)))
+
+    def upload_diagonals(self, diags: np.ndarray, stride: int = 1, level: int | None = None) -> Diagonals:
+        diags = np.ascontiguousarray(diags, dtype=np.uint64)
+        level = level if level is not None else diags.shape[1] - self.k
+        h = ctypes.c_void_p()
+        check(lib().ckks_upload_diagonals(self.h, ctypes.byref(h), diags.shape[0], 0, stride, level,
+                                          _ptr(diags), diags.size))
+        return Diagonals(self, h, diags.shape[0], stride, level)
+
+    def upload_diagonals_device(self, diags_t, stride: int = 1, level: int | None = None, stream=None) -> Diagonals:
+        """diags_t: device tensor [n_diag][level + k][N] (copied by the library)."""
+        level = level if level is not None else diags_t.shape[1] - self.k
+        h = ctypes.c_void_p()
+        check(lib().ckks_upload_diagonals_device(self.h, ctypes.byref(h), diags_t.shape[0], 0, stride, level,
+                                                 _ptr(diags_t), diags_t.numel(), _stream(stream)))
+        return Diagonals(self, h, diags_t.shape[0], stride, level)
+
+    def required_rotations(self, algo: str, split, n_diag: int, stride: int = 1) -> list:
+        sp = Split(*(tuple(split) + (0,) * (3 - len(split)))) if split else None
+        buf = (ctypes.c_int32 * 4096)()
+        n = lib().lt_required_rotations(self.h, ALGOS[algo], ctypes.byref(sp) if sp else None, n_diag, stride,
+                                        buf, 4096)
+        if n < 0:
+            raise CkksError(1, "bad split")
+        return list(buf[:n])
+
+    def choose_split(self, algo: str, level: int, n_diag: int):
+        sp = Split()
+        check(lib().lt_choose_split(self.h, ALGOS[algo], level, n_diag, ctypes.byref(sp)))
+        return sp.tuple()
+
+    # ----------------------------------------------------------- ciphertexts
+    def ct_empty(self, level: int) -> Ciphertext:
+        torch = _torch()
+        t = torch.empty((2, level, self.N), dtype=torch.int64, device=f"cuda:{self.device}")
+        return self.ct_wrap(t, level)
+
+    def ct_wrap(self, tensor, level: int) -> Ciphertext:
+        h = ctypes.c_void_p()
+        check(lib().ckks_ct_wrap_device(self.h, ctypes.byref(h), level, _ptr(tensor)))
+        return Ciphertext(h, level, tensor, self)
+
+    def ct_from_host(self, c: np.ndarray) -> Ciphertext:
+        c = np.ascontiguousarray(c, dtype=np.uint64)
+        return self.ct_wrap(to_device(c, f"cuda:{self.device}"), c.shape[1])
+
+    def ct_upload(self, c: np.ndarray) -> Ciphertext:
+        """Library-owned device copy (ckks_ct_upload)."""
+        c = np.ascontiguousarray(c, dtype=np.uint64)
+        h = ctypes.c_void_p()
+        check(lib().ckks_ct_upload(self.h, ctypes.byref(h), c.shape[1], _ptr(c)))
+        return Ciphertext(h, c.shape[1], None, self)
+
+    def ct_create(self, level: int) -> Ciphertext:
+        h = ctypes.c_void_p()
+        check(lib().ckks_ct_create(self.h, ctypes.byref(h), level))
+        return Ciphertext(h, level, None, self)
+
+    def h2d_async(self, ct: Ciphertext, host: np.ndarray, stream=None) -> None:
+        check(lib().ckks_ct_h2d_async(ct.handle, _ptr(host), host.size, _stream(stream)))
+
+    def d2h_async(self, ct: Ciphertext, host: np.ndarray, stream=None) -> None:
+        check(lib().ckks_ct_d2h_async(ct.handle, _ptr(host), host.size, _stream(stream)))
+
+    # ----------------------------------------------------------- the LT
+    def lt_eval(self, ct: Ciphertext, diags: Diagonals, algo: str = "th", split=None, out: Ciphertext | None = None,
+                stream=None):
+        out = out or self.ct_empty(ct.level - 1)
+        sp = Split(*(tuple(split) + (1,) * (3 - len(split)))) if split else Split(0, 0, 0)
+        chosen = Split()
+        check(lib().lt_eval(self.h, ct.handle, diags.handle, ALGOS[algo], ctypes.byref(sp), out.handle,
+                            _stream(stream), ctypes.byref(chosen)))
+        return out, chosen.tuple()
+
+    def lt_eval_batch(self, cts, diags, algos=None, splits=None, outs=None, stream=None):
+        n = len(cts)
+        outs = outs or [self.ct_empty(c.level - 1) for c in cts]
+        arr = lambda xs: (ctypes.c_void_p * n)(*[x.handle for x in xs])
+        al = (ctypes.c_int * n)(*[ALGOS[a] for a in algos]) if algos else None
+        sp = None
+        if splits:
+            sp = (Split * n)(*[Split(*(tuple(s) + (1,) * (3 - len(s)))) for s in splits])
+        check(lib().lt_eval_batch(self.h, n, arr(cts), arr(diags), al, sp, arr(outs), _stream(stream)))
+        return outs
+
+    # ----------------------------------------------------------- steps (device tensors)
+    def ntt(self, poly, level: int, ext: bool, inverse: bool, stream=None):
+        check(lib().ckks_poly_ntt(self.h, _ptr(poly), level, int(ext), int(inverse), _stream(stream)))
+
+    def decompose(self, c, level: int, rot: int = 0, digits=None, stream=None):
+        torch = _torch()
+        if digits is None:
+            digits = torch.empty((self.beta(level), level + self.k, self.N), dtype=torch.int64, device=c.device)
+        check(lib().ckks_decompose(self.h, level, _ptr(c), rot, _ptr(digits), _stream(stream)))
+        return digits
+
+    def ks_inner(self, level: int, digits, key_rot: int, rot: int, x0=None, lift_x0: bool = False,
+                 out0=None, out1=None, accumulate: bool = False, stream=None):
+        torch = _torch()
+        shape = (level + self.k, self.N)
+        out0 = out0 if out0 is not None else torch.empty(shape, dtype=torch.int64, device=digits.device)
+        out1 = out1 if out1 is not None else torch.empty(shape, dtype=torch.int64, device=digits.device)
+        check(lib().ckks_ks_inner(self.h, level, _ptr(digits), key_rot, rot, _ptr(x0), int(lift_x0), _ptr(out0),
+                                  _ptr(out1), int(accumulate), _stream(stream)))
+        return out0, out1
+
+    def moddown(self, x, level: int, out=None, stream=None):
+        torch = _torch()
+        out = out if out is not None else torch.empty((level, self.N), dtype=torch.int64, device=x.device)
+        check(lib().ckks_moddown(self.h, level, _ptr(x), _ptr(out), _stream(stream)))
+        return out
+
+    def moddown_rescale(self, x, level: int, out=None, stream=None):
+        torch = _torch()
+        out = out if out is not None else torch.empty((level - 1, self.N), dtype=torch.int64, device=x.device)
+        check(lib().ckks_moddown_rescale(self.h, level, _ptr(x), _ptr(out), _stream(stream)))
+        return out
+
+    def rescale(self, x, level: int, out=None, stream=None):
+        torch = _torch()
+        out = out if out is not None else torch.empty((level - 1, self.N), dtype=torch.int64, device=x.device)
+        check(lib().ckks_rescale(self.h, level, _ptr(x), _ptr(out), _stream(stream)))
+        return out
+
+    def automorphism(self, x, rot: int, out=None, stream=None):
+        torch = _torch()
+        out = out if out is not None else torch.empty_like(x)
+        check(lib().ckks_automorphism(self.h, x.numel() // self.N, _ptr(x), rot, _ptr(out), _stream(stream)))
+        return out
+
+
+def kernel_launches() -> int:
+    return int(lib().ckks_kernel_launch_count())
+
+
+def profile_enable(kernel_class: str, on: bool = True) -> None:
+    L = lib()
+    L.ckks_profile_enable.argtypes = [ctypes.c_char_p, ctypes.c_int]
+    check(L.ckks_profile_enable(kernel_class.encode(), int(on)))
+
+
+def profile_read(kernel_class: str):
+    """(total device ms, launches) of a kernel class since the last reset."""
+    L = lib()
+    L.ckks_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_uint64)]
+    ms, n = ctypes.c_double(), ctypes.c_uint64()
+    check(L.ckks_profile_read(kernel_class.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def profile_reset() -> None:
+    lib().ckks_profile_reset()
+
+
+KERNEL_CLASSES = ["diag_mac", "ks_inner", "ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols",
+                  "automorphism", "add_gather"]

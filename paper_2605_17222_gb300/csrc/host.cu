@@ -1,0 +1,1073 @@
+// Host side of the library: context constants, device memory, the key
+// switching steps (Fig. 1), the four LT schedules and the C ABI of
+// include/ckks_lt.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ckks_lt.h"
+#include "kernels.h"
+
+using namespace ckks;
+typedef unsigned __int128 u128;
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_err;
+
+namespace {
+
+struct Fail {
+    ckks_status st;
+};
+
+[[noreturn]] void fail(ckks_status st, const std::string& msg) {
+    g_err = msg;
+    throw Fail{st};
+}
+
+void cuda_check(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) fail(e == cudaErrorMemoryAllocation ? CKKS_ENOMEM : CKKS_ECUDA,
+                               std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(x) cuda_check((x), #x)
+
+template <typename F>
+ckks_status guarded(F&& f) {
+    try {
+        f();
+        return CKKS_OK;
+    } catch (const Fail& e) {
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        g_err = "host allocation failed";
+        return CKKS_ENOMEM;
+    } catch (...) {
+        g_err = "unexpected exception";
+        return CKKS_EINVAL;
+    }
+}
+
+// ------------------------------------------------------------------ host modular arithmetic
+u64 mulmod_h(u64 a, u64 b, u64 q) { return (u64)((u128)a * b % q); }
+u64 powmod_h(u64 a, u64 e, u64 q) {
+    u64 r = 1 % q;
+    a %= q;
+    while (e) {
+        if (e & 1) r = mulmod_h(r, a, q);
+        a = mulmod_h(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+u64 invmod_h(u64 a, u64 q) { return powmod_h(a % q, q - 2, q); }  // q prime
+u64 shoup_h(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+bool is_prime_h(u64 n) {
+    if (n < 2) return false;
+    static const u64 bases[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    for (u64 p : bases)
+        if (n % p == 0) return n == p;
+    u64 d = n - 1;
+    int s = 0;
+    while (!(d & 1)) d >>= 1, s++;
+    for (u64 a : bases) {
+        u64 x = powmod_h(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int r = 1; r < s; r++) {
+            x = mulmod_h(x, x, n);
+            if (x == n - 1) {
+                comp = false;
+                break;
+            }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+ModC modc_h(u64 q) {
+    u128 mu = (~(u128)0) / q;  // = floor(2^128 / q) since q does not divide 2^128
+    return ModC{q, (u64)(mu >> 64), (u64)mu};
+}
+
+u32 brv_h(u32 x, u32 bits) {
+    u32 r = 0;
+    for (u32 i = 0; i < bits; i++) r = (r << 1) | ((x >> i) & 1);
+    return r;
+}
+
+// ------------------------------------------------------------------ device buffers
+struct DevBuf {
+    u64* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct LevelConsts {
+    // Decompose: per Q limb j, N^-1 (Q_b/q_j)^-1 mod q_j; table [beta][ext][alpha] of [Q_b/q_j]_t
+    std::vector<u64> dec_c, dec_sh;
+    u64* dec_tab = nullptr;
+    // ModDown: per P limb, N^-1 (P/p_i)^-1; table [level][k] of [P/p_i]_{q_j}; P^-1 mod q_j
+    std::vector<u64> md_c, md_sh, md_pinv, md_pinv_sh;
+    u64* md_tab = nullptr;
+    // ModDown+rescale over {q_{l-1}, p_0..}: same shapes with k+1 sources, level-1 targets
+    std::vector<u64> mdr_c, mdr_sh, mdr_pinv, mdr_pinv_sh;
+    u64* mdr_tab = nullptr;
+    // rescale: source q_{l-1}
+    std::vector<u64> rs_c, rs_sh, rs_inv, rs_inv_sh;
+    u64* rs_tab = nullptr;
+};
+
+struct ckks_ctx {
+    int device = 0;
+    u32 log_n = 0, N = 0, L = 0, K = 0, dnum = 0, alpha = 0, beta_max = 0;
+    std::vector<u64> mods;  // q_0..q_{L-1}, p_0..p_{K-1}
+    DevBuf d_mods, d_psi, d_psi_sh, d_ipsi, d_ipsi_sh, d_lift, d_lift_sh;
+    NttTables T{};
+    std::map<u32, LevelConsts> levels;
+    std::map<u32, u64*> keys;  // rotation (mod N/2) -> [beta_max][2][L+K][N]
+    std::mutex mu;
+    size_t bytes = 0;
+
+    u32 beta(u32 level) const { return (level + alpha - 1) / alpha; }
+    u32 slots() const { return N / 2; }
+    size_t key_words() const { return (size_t)beta_max * 2 * (L + K) * N; }
+    u32 gmod(u32 level, u32 t) const { return t < level ? t : L + (t - level); }
+    u32 galois(int64_t r) const {
+        int64_t rr = r % (int64_t)slots();
+        if (rr < 0) rr += slots();
+        return (u32)powmod_h(5, (u64)rr, 2ull * N);
+    }
+    u32 rotkey(int64_t r) const {
+        int64_t rr = r % (int64_t)slots();
+        if (rr < 0) rr += slots();
+        return (u32)rr;
+    }
+
+    u64* dalloc(size_t words) {
+        void* p = nullptr;
+        CK(cudaMalloc(&p, words * sizeof(u64)));
+        bytes += words * sizeof(u64);
+        return (u64*)p;
+    }
+    void dfree(u64* p, size_t words) {
+        if (p) {
+            cudaFree(p);
+            bytes -= words * sizeof(u64);
+        }
+    }
+    u64* upload(const std::vector<u64>& v) {
+        u64* p = dalloc(v.size());
+        CK(cudaMemcpy(p, v.data(), v.size() * sizeof(u64), cudaMemcpyHostToDevice));
+        return p;
+    }
+
+    const LevelConsts& lc(u32 level);
+};
+
+struct ckks_ct {
+    ckks_ctx* ctx;
+    u32 level;
+    u64* d;
+    bool owned;
+};
+
+struct ckks_diags {
+    ckks_ctx* ctx;
+    u32 n_diag, level;
+    int32_t offset0, stride;
+    u64* d;
+};
+
+// Constants that depend on the level (digit boundaries, sources of the
+// merged rescale), computed on first use.
+const LevelConsts& ckks_ctx::lc(u32 level) {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = levels.find(level);
+    if (it != levels.end()) return it->second;
+    LevelConsts c;
+    const u32 ext = level + K, beta = this->beta(level);
+    auto modof = [&](u32 t) { return mods[gmod(level, t)]; };
+    // Decompose, Eq. (3) per digit
+    c.dec_c.resize(level);
+    c.dec_sh.resize(level);
+    std::vector<u64> dt((size_t)beta * ext * alpha, 0);
+    for (u32 b = 0; b < beta; b++) {
+        const u32 first = b * alpha, cnt = std::min(alpha, level - first);
+        for (u32 jj = 0; jj < cnt; jj++) {
+            const u32 j = first + jj;
+            const u64 qj = mods[j];
+            u64 qhat = 1;
+            for (u32 ii = 0; ii < cnt; ii++)
+                if (ii != jj) qhat = mulmod_h(qhat, mods[first + ii] % qj, qj);
+            const u64 v = mulmod_h(invmod_h(N % qj, qj), invmod_h(qhat, qj), qj);
+            c.dec_c[j] = v;
+            c.dec_sh[j] = shoup_h(v, qj);
+            for (u32 t = 0; t < ext; t++) {
+                if (t >= first && t < first + cnt) continue;
+                const u64 mt = modof(t);
+                u64 h = 1;
+                for (u32 ii = 0; ii < cnt; ii++)
+                    if (ii != jj) h = mulmod_h(h, mods[first + ii] % mt, mt);
+                dt[((size_t)b * ext + t) * alpha + jj] = h;
+            }
+        }
+    }
+    c.dec_tab = upload(dt);
+    // generic "modulus switch down" constants for a source set S and target limbs 0..ntgt-1
+    auto down = [&](const std::vector<u32>& srcg, u32 ntgt, std::vector<u64>& sc, std::vector<u64>& ssh,
+                    std::vector<u64>& pinv, std::vector<u64>& pinv_sh, u64*& tab) {
+        const u32 ns = (u32)srcg.size();
+        sc.resize(ns);
+        ssh.resize(ns);
+        for (u32 i = 0; i < ns; i++) {
+            const u64 pi = mods[srcg[i]];
+            u64 hat = 1;
+            for (u32 o = 0; o < ns; o++)
+                if (o != i) hat = mulmod_h(hat, mods[srcg[o]] % pi, pi);
+            const u64 v = mulmod_h(invmod_h(N % pi, pi), invmod_h(hat, pi), pi);
+            sc[i] = v;
+            ssh[i] = shoup_h(v, pi);
+        }
+        std::vector<u64> tb((size_t)ntgt * ns);
+        pinv.resize(ntgt);
+        pinv_sh.resize(ntgt);
+        for (u32 j = 0; j < ntgt; j++) {
+            const u64 qj = mods[j];
+            u64 prod = 1;
+            for (u32 i = 0; i < ns; i++) {
+                u64 hat = 1;
+                for (u32 o = 0; o < ns; o++)
+                    if (o != i) hat = mulmod_h(hat, mods[srcg[o]] % qj, qj);
+                tb[(size_t)j * ns + i] = hat;
+                prod = mulmod_h(prod, mods[srcg[i]] % qj, qj);
+            }
+            pinv[j] = invmod_h(prod, qj);
+            pinv_sh[j] = shoup_h(pinv[j], qj);
+        }
+        tab = upload(tb);
+    };
+    std::vector<u32> P;
+    for (u32 i = 0; i < K; i++) P.push_back(L + i);
+    down(P, level, c.md_c, c.md_sh, c.md_pinv, c.md_pinv_sh, c.md_tab);
+    if (level >= 2) {
+        std::vector<u32> S{level - 1};
+        for (u32 i = 0; i < K; i++) S.push_back(L + i);
+        down(S, level - 1, c.mdr_c, c.mdr_sh, c.mdr_pinv, c.mdr_pinv_sh, c.mdr_tab);
+        down(std::vector<u32>{level - 1}, level - 1, c.rs_c, c.rs_sh, c.rs_inv, c.rs_inv_sh, c.rs_tab);
+    }
+    return levels.emplace(level, std::move(c)).first->second;
+}
+
+// ------------------------------------------------------------------ stream-ordered scratch
+namespace {
+
+struct Arena {
+    cudaStream_t st;
+    std::vector<void*> blocks;
+    size_t limb_words;
+    explicit Arena(cudaStream_t s, size_t lw) : st(s), limb_words(lw) {}
+    u64* limbs(size_t n) {
+        void* p = nullptr;
+        CK(cudaMallocAsync(&p, std::max<size_t>(1, n) * limb_words * sizeof(u64), st));
+        blocks.push_back(p);
+        return (u64*)p;
+    }
+    ~Arena() {
+        for (void* p : blocks) cudaFreeAsync(p, st);
+    }
+};
+
+// ------------------------------------------------------------------ key switching steps
+// Decompose (Fig. 1, Eq. 3): c [level][N] (gathered through x -> x^gal if gal)
+// -> digits [beta][level+K][N].  Y: scratch [level][N].
+void op_decompose(ckks_ctx* C, u32 level, const u64* c, u32 gal, u64* digits, u64* Y, cudaStream_t st) {
+    const LevelConsts& LC = C->lc(level);
+    const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
+    std::vector<InvJob> ij(level);
+    for (u32 j = 0; j < level; j++)
+        ij[j] = InvJob{c + (size_t)j * N, Y + (size_t)j * N, Y + (size_t)j * N, LC.dec_c[j], LC.dec_sh[j], j, gal};
+    launch_inv_ntt(C->T, ij.data(), level, st);
+    std::vector<FwdJob> fj;
+    for (u32 b = 0; b < beta; b++) {
+        const u32 first = b * C->alpha, cnt = std::min(C->alpha, level - first);
+        for (u32 t = 0; t < ext; t++) {
+            if (t >= first && t < first + cnt) continue;
+            fj.push_back(FwdJob{Y + (size_t)first * N, digits + ((size_t)b * ext + t) * N,
+                                LC.dec_tab + ((size_t)b * ext + t) * C->alpha, nullptr, nullptr, 0, 0,
+                                C->gmod(level, t), cnt});
+        }
+    }
+    launch_fwd_ntt(C->T, fj.data(), (int)fj.size(), st);
+    for (u32 b = 0; b < beta; b++) {
+        const u32 first = b * C->alpha, cnt = std::min(C->alpha, level - first);
+        u64* dst = digits + ((size_t)b * ext + first) * N;
+        if (gal) launch_automorphism(c + (size_t)first * N, dst, cnt, gal, C->log_n, st);
+        else CK(cudaMemcpyAsync(dst, c + (size_t)first * N, (size_t)cnt * N * 8, cudaMemcpyDeviceToDevice, st));
+    }
+}
+
+// Modulus switch down over a contiguous source run of x: INTT the sources
+// (scaled), basis-convert to the targets 0..ntgt-1 fused into the forward NTT,
+// and finish with out = (x_j - conv_j) * inv_j (Eq. 4 / Eq. 1).
+void op_down(ckks_ctx* C, u32 level, const u64* x, u32 src_first, const std::vector<u32>& src_g,
+             const std::vector<u64>& sc, const std::vector<u64>& ssh, const u64* tab, u32 ntgt,
+             const std::vector<u64>& inv, const std::vector<u64>& inv_sh, u64* out, u64* Y, cudaStream_t st) {
+    const u32 N = C->N, ns = (u32)src_g.size();
+    std::vector<InvJob> ij(ns);
+    for (u32 i = 0; i < ns; i++)
+        ij[i] = InvJob{x + (size_t)(src_first + i) * N, Y + (size_t)i * N, Y + (size_t)i * N, sc[i], ssh[i], src_g[i], 0};
+    launch_inv_ntt(C->T, ij.data(), ns, st);
+    std::vector<FwdJob> fj(ntgt);
+    for (u32 j = 0; j < ntgt; j++)
+        fj[j] = FwdJob{Y, out + (size_t)j * N, tab + (size_t)j * ns, x + (size_t)j * N, out + (size_t)j * N,
+                       inv[j], inv_sh[j], j, ns};
+    launch_fwd_ntt(C->T, fj.data(), (int)ntgt, st);
+}
+
+void op_moddown(ckks_ctx* C, u32 level, const u64* x, u64* out, u64* Y, cudaStream_t st) {
+    const LevelConsts& LC = C->lc(level);
+    std::vector<u32> g;
+    for (u32 i = 0; i < C->K; i++) g.push_back(C->L + i);
+    op_down(C, level, x, level, g, LC.md_c, LC.md_sh, LC.md_tab, level, LC.md_pinv, LC.md_pinv_sh, out, Y, st);
+}
+
+void op_moddown_rescale(ckks_ctx* C, u32 level, const u64* x, u64* out, u64* Y, cudaStream_t st) {
+    const LevelConsts& LC = C->lc(level);
+    std::vector<u32> g{level - 1};
+    for (u32 i = 0; i < C->K; i++) g.push_back(C->L + i);
+    op_down(C, level, x, level - 1, g, LC.mdr_c, LC.mdr_sh, LC.mdr_tab, level - 1, LC.mdr_pinv, LC.mdr_pinv_sh, out,
+            Y, st);
+}
+
+void op_rescale(ckks_ctx* C, u32 level, const u64* x, u64* out, u64* Y, cudaStream_t st) {
+    const LevelConsts& LC = C->lc(level);
+    op_down(C, level, x, level - 1, std::vector<u32>{level - 1}, LC.rs_c, LC.rs_sh, LC.rs_tab, level - 1, LC.rs_inv,
+            LC.rs_inv_sh, out, Y, st);
+}
+
+const u64* key_of(ckks_ctx* C, int64_t r) {
+    auto it = C->keys.find(C->rotkey(r));
+    if (it == C->keys.end()) fail(CKKS_ENOKEY, "missing rotation key for r = " + std::to_string(C->rotkey(r)));
+    return it->second;
+}
+
+void op_ks_inner(ckks_ctx* C, u32 level, const u64* digits, const u64* key, u32 gal, const u64* x0, int x0_mode,
+                 u64* out0, u64* out1, int acc, cudaStream_t st) {
+    KsArgs a{};
+    a.digits = digits;
+    a.key = key;
+    a.x0 = x0;
+    a.out0 = out0;
+    a.out1 = out1;
+    a.mods = (const ModC*)C->d_mods.p;
+    a.lift_c = C->d_lift.p;
+    a.lift_sh = C->d_lift_sh.p;
+    a.level = level;
+    a.ext = level + C->K;
+    a.L = C->L;
+    a.beta = C->beta(level);
+    a.beta_max = C->beta_max;
+    a.gal = gal;
+    a.x0_mode = x0 ? x0_mode : 0;
+    a.accumulate = acc;
+    a.log_n = C->log_n;
+    launch_ks_inner(a, st);
+}
+
+void op_add_gather(ckks_ctx* C, u32 nlimbs, u32 level, const u64* a, const u64* b, u64* out, u32 gal, int acc,
+                   cudaStream_t st) {
+    std::vector<AddJob> j(nlimbs);
+    for (u32 t = 0; t < nlimbs; t++)
+        j[t] = AddJob{a + (size_t)t * C->N, b ? b + (size_t)t * C->N : nullptr, out + (size_t)t * C->N,
+                      C->gmod(level, t), 0};
+    launch_add_gather((const ModC*)C->d_mods.p, j.data(), (int)nlimbs, gal, acc, C->log_n, st);
+}
+
+DiagMacArgs dm_base(ckks_ctx* C, u32 level, bool with_p, const ckks_diags* f) {
+    DiagMacArgs a;
+    memset(&a, 0, sizeof(a));
+    a.mods = (const ModC*)C->d_mods.p;
+    a.lift_c = C->d_lift.p;
+    a.lift_sh = C->d_lift_sh.p;
+    a.diags = f->d;
+    a.level = level;
+    a.ext = level + (with_p ? C->K : 0);
+    a.L = C->L;
+    a.k_p = C->K;
+    a.beta = C->beta(level);
+    a.log_n = C->log_n;
+    a.diag_level = f->level;
+    return a;
+}
+
+// ------------------------------------------------------------------ the four schedules
+struct LtIO {
+    const u64* c0;
+    const u64* c1;
+    u64* o0;
+    u64* o1;
+};
+
+// TH-BSGS, Algorithm 2 (n1, n2, n3 = n'1, n'2, n'3).  DH-BSGS (Algorithm 1)
+// is the case n1 = 1 with (n2, n3) = (n1, n2) of Algorithm 1, and the hoisted
+// diagonal method the case (1, D, 1): the three share this schedule and give
+// identical residues for those splits.
+void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 n2, u32 n3, cudaStream_t st) {
+    const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
+    const int64_t s = f->stride;
+    Arena ar(st, N);
+    u64* Y = ar.limbs(std::max(level, C->K + 1));
+    std::vector<u64*> A(n1, nullptr), B(n1, nullptr), Dg(n1, nullptr);
+    Dg[0] = ar.limbs((size_t)beta * ext);
+    op_decompose(C, level, io.c1, 0, Dg[0], Y, st);  // line 1
+    u64* Tq = (n1 > 1 || n3 > 1) ? ar.limbs(level) : nullptr;
+    for (u32 i = 1; i < n1; i++) {  // lines 3-7
+        const int64_t r = s * i;
+        A[i] = ar.limbs(ext);
+        B[i] = ar.limbs(ext);
+        op_ks_inner(C, level, Dg[0], key_of(C, r), C->galois(r), io.c0, 2, A[i], B[i], 0, st);
+        if (n2 > 1) {
+            Dg[i] = ar.limbs((size_t)beta * ext);
+            op_moddown(C, level, B[i], Tq, Y, st);
+            op_decompose(C, level, Tq, 0, Dg[i], Y, st);
+        }
+    }
+    DiagMacArgs a = dm_base(C, level, true, f);
+    a.n1 = n1;
+    a.n2 = n2;
+    a.n3 = n3;
+    a.lift0 = 1;
+    a.A[0] = io.c0;
+    a.B[0] = io.c1;
+    for (u32 i = 1; i < n1; i++) a.A[i] = A[i], a.B[i] = B[i];
+    for (u32 i = 0; i < n1; i++) a.Dg[i] = Dg[i];
+    for (u32 j = 1; j < n2; j++) {
+        a.keys[j] = key_of(C, s * n1 * j);
+        a.gal_mid[j] = C->galois(s * n1 * j);
+    }
+    std::vector<u64*> U0(n3), U1(n3);
+    for (u32 k = 0; k < n3; k++) {
+        U0[k] = ar.limbs(ext);
+        U1[k] = ar.limbs(ext);
+        a.U0[k] = U0[k];
+        a.U1[k] = U1[k];
+        a.gal_diag[k] = k ? C->galois(-s * n1 * n2 * k) : 0;
+    }
+    launch_diag_mac(a, st);  // lines 8-14
+    u64* Dk = n3 > 1 ? ar.limbs((size_t)beta * ext) : nullptr;
+    for (u32 k = 1; k < n3; k++) {  // lines 15-18
+        const int64_t r = s * n1 * n2 * k;
+        op_moddown(C, level, U1[k], Tq, Y, st);
+        op_decompose(C, level, Tq, 0, Dk, Y, st);
+        op_ks_inner(C, level, Dk, key_of(C, r), C->galois(r), U0[k], 1, U0[0], U1[0], 1, st);
+    }
+    op_moddown_rescale(C, level, U0[0], io.o0, Y, st);  // line 19
+    op_moddown_rescale(C, level, U1[0], io.o1, Y, st);
+}
+
+// BSGS, Eq. (5): un-hoisted rotations (each with its own Decompose of the
+// rotated c1 and two ModDowns), products over Q, plain rescale at the end.
+void sched_bsgs(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 n2, cudaStream_t st) {
+    const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
+    const int64_t s = f->stride;
+    Arena ar(st, N);
+    u64* Y = ar.limbs(std::max(level, C->K + 1));
+    u64* D = ar.limbs((size_t)beta * ext);
+    u64* X0 = ar.limbs(ext);
+    u64* X1 = ar.limbs(ext);
+    u64* T0 = ar.limbs(level);
+    auto rotate_into = [&](const u64* c0, const u64* c1, int64_t r, u64* o0, u64* o1, int acc) {
+        const u32 g = C->galois(r);
+        op_decompose(C, level, c1, g, D, Y, st);
+        op_ks_inner(C, level, D, key_of(C, r), 0, nullptr, 0, X0, X1, 0, st);
+        op_moddown(C, level, X0, T0, Y, st);
+        if (acc) {
+            op_add_gather(C, level, level, c0, T0, o0, g, 1, st);
+            op_moddown(C, level, X1, X0, Y, st);  // reuse X0 as [level] scratch
+            op_add_gather(C, level, level, X0, nullptr, o1, 0, 1, st);
+        } else {
+            op_add_gather(C, level, level, c0, T0, o0, g, 0, st);
+            op_moddown(C, level, X1, o1, Y, st);
+        }
+    };
+    DiagMacArgs a = dm_base(C, level, false, f);
+    a.n1 = n1;
+    a.n2 = 1;
+    a.n3 = n2;
+    a.A[0] = io.c0;
+    a.B[0] = io.c1;
+    for (u32 i = 1; i < n1; i++) {
+        u64* c0 = ar.limbs(level);
+        u64* c1 = ar.limbs(level);
+        rotate_into(io.c0, io.c1, s * i, c0, c1, 0);
+        a.A[i] = c0;
+        a.B[i] = c1;
+    }
+    std::vector<u64*> V0(n2), V1(n2);
+    for (u32 j = 0; j < n2; j++) {
+        V0[j] = ar.limbs(level);
+        V1[j] = ar.limbs(level);
+        a.U0[j] = V0[j];
+        a.U1[j] = V1[j];
+        a.gal_diag[j] = j ? C->galois(-s * n1 * j) : 0;
+    }
+    launch_diag_mac(a, st);
+    for (u32 j = 1; j < n2; j++) rotate_into(V0[j], V1[j], s * n1 * j, V0[0], V1[0], 1);
+    op_rescale(C, level, V0[0], io.o0, Y, st);
+    op_rescale(C, level, V1[0], io.o1, Y, st);
+}
+
+void validate_split(lt_algo algo, u32 D, const lt_split& sp) {
+    switch (algo) {
+        case LT_DIAG: break;
+        case LT_BSGS:
+        case LT_DH_BSGS:
+            if (sp.n1 < 1 || sp.n2 < 1 || (sp.n3 != 1 && sp.n3 != 0) || sp.n1 * sp.n2 != D)
+                fail(CKKS_EINVAL, "BSGS/DH split needs n1*n2 = n_diag and n3 = 1");
+            if (sp.n1 > (u32)DM_MAX_N1 || sp.n2 > (u32)DM_MAX_N3) fail(CKKS_EINVAL, "split exceeds kernel limits");
+            break;
+        case LT_TH_BSGS:
+            if (sp.n1 < 1 || sp.n2 < 1 || sp.n3 < 1 || sp.n1 * sp.n2 * sp.n3 != D)
+                fail(CKKS_EINVAL, "TH split needs n1*n2*n3 = n_diag");
+            if (sp.n1 > (u32)DM_MAX_N1 || sp.n2 > (u32)DM_MAX_N2 || sp.n3 > (u32)DM_MAX_N3)
+                fail(CKKS_EINVAL, "split exceeds kernel limits");
+            break;
+        default: fail(CKKS_EINVAL, "unknown algorithm");
+    }
+    if (algo == LT_DIAG && D > (u32)DM_MAX_N2) fail(CKKS_EINVAL, "too many diagonals for the diagonal method");
+}
+
+std::vector<int64_t> rotations(lt_algo algo, const lt_split& sp, u32 D) {
+    std::vector<int64_t> r;
+    if (algo == LT_DIAG) {
+        for (u32 t = 1; t < D; t++) r.push_back(t);
+    } else if (algo == LT_BSGS || algo == LT_DH_BSGS) {
+        for (u32 i = 1; i < sp.n1; i++) r.push_back(i);
+        for (u32 j = 1; j < sp.n2; j++) r.push_back((int64_t)sp.n1 * j);
+    } else {
+        for (u32 i = 1; i < sp.n1; i++) r.push_back(i);
+        for (u32 j = 1; j < sp.n2; j++) r.push_back((int64_t)sp.n1 * j);
+        for (u32 k = 1; k < sp.n3; k++) r.push_back((int64_t)sp.n1 * sp.n2 * k);
+    }
+    return r;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ split choice (autotuner model)
+// Time model of one LT on this GPU: HBM bytes that must move (keys, diagonals,
+// ciphertexts, plus the digits the fused diagonal kernel re-reads) over the
+// HBM bandwidth, plus the modular multiplications of the NTT-heavy steps
+// over the integer rate.  The split with the smallest estimate wins; ties go
+// to fewer keys.  Rates are measured figures of the GB300 kernels here.
+namespace {
+double model_time(const ckks_ctx* C, lt_algo algo, u32 level, u32 D, const lt_split& sp) {
+    const double limb = 8.0 * C->N, ext = level + C->K, beta = (double)((level + C->alpha - 1) / C->alpha);
+    const double bw = 5.5e12, ntt_rate = 9.0e11;  // bytes/s, butterflies/s
+    const double ntt = (C->N / 2.0) * C->log_n;
+    double keys, dec, md, kspairs;
+    if (algo == LT_TH_BSGS) {
+        keys = sp.n1 + sp.n2 + sp.n3 - 3;
+        dec = sp.n1 + sp.n3 - 1;
+        md = sp.n1 + sp.n3;
+        kspairs = (double)sp.n1 * sp.n2 + sp.n3 - 2;
+    } else if (algo == LT_DH_BSGS) {
+        keys = sp.n1 + sp.n2 - 2;
+        dec = sp.n2;
+        md = sp.n2 + 1;
+        kspairs = sp.n1 + sp.n2 - 2;
+    } else if (algo == LT_BSGS) {
+        keys = sp.n1 + sp.n2 - 2;
+        dec = keys;
+        md = 2 * keys;
+        kspairs = keys;
+    } else {
+        keys = D - 1;
+        dec = 1;
+        md = 2;
+        kspairs = D - 1;
+    }
+    double bytes = limb * (D * ext + keys * 2 * beta * ext + 4 * level);
+    // digits re-read by the middle layer and the decompose outputs
+    bytes += limb * dec * beta * ext * 2.0;
+    double flops = dec * (level + beta * (ext - C->alpha)) * ntt + md * (C->K + level) * ntt;
+    double mac = (kspairs * 2 * beta * ext + 2.0 * D * ext) * C->N;
+    return bytes / bw + flops / ntt_rate + mac / 2.0e12;
+}
+}  // namespace
+
+static lt_split choose_split(const ckks_ctx* C, lt_algo algo, u32 level, u32 D) {
+    lt_split best{0, 0, 0};
+    if (algo == LT_DIAG) return lt_split{1, D, 1};
+    double bt = 1e300;
+    std::vector<u32> divs;
+    for (u32 d = 1; d <= D; d++)
+        if (D % d == 0) divs.push_back(d);
+    for (u32 a : divs)
+        for (u32 b : divs) {
+            if ((u64)a * b > D || D % ((u64)a * b)) continue;
+            lt_split sp;
+            if (algo == LT_TH_BSGS) {
+                sp = lt_split{a, b, D / (a * b)};
+                if (sp.n1 > (u32)DM_MAX_N1 || sp.n3 > (u32)DM_MAX_N3 || sp.n2 > (u32)DM_MAX_N2) continue;
+            } else {
+                if (a * b != D) continue;
+                sp = lt_split{a, b, 1};
+                if (sp.n1 > (u32)DM_MAX_N1 || sp.n2 > (u32)DM_MAX_N3) continue;
+            }
+            const double t = model_time(C, algo, level, D, sp);
+            if (t < bt) bt = t, best = sp;
+        }
+    return best;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* ckks_last_error(void) { return g_err.c_str(); }
+
+ckks_status ckks_profile_enable(const char* kernel_class, int on) {
+    return guarded([&] {
+        const int c = prof_class(kernel_class);
+        if (c < 0) fail(CKKS_EINVAL, "unknown kernel class");
+        prof_enable(c, on != 0);
+    });
+}
+
+ckks_status ckks_profile_read(const char* kernel_class, double* total_ms, uint64_t* launches) {
+    return guarded([&] {
+        const int c = prof_class(kernel_class);
+        if (c < 0 || !total_ms || !launches) fail(CKKS_EINVAL, "unknown kernel class or null output");
+        prof_read(c, total_ms, launches);
+    });
+}
+
+void ckks_profile_reset(void) { prof_reset(); }
+uint64_t ckks_kernel_launch_count(void) { return ckks::launches(); }
+size_t ckks_device_bytes_in_use(const ckks_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+ckks_status ckks_ctx_create(ckks_ctx** out, uint32_t log_n, const uint64_t* q, uint32_t n_q, const uint64_t* p,
+                            uint32_t n_p, uint32_t dnum, int device) {
+    return guarded([&] {
+        if (!out || !q || !p) fail(CKKS_EINVAL, "null argument");
+        *out = nullptr;
+        if (log_n < 10 || log_n > 17) fail(CKKS_EINVAL, "log_n must be in [10, 17]");
+        if (n_q < 2 || n_p < 1 || dnum < 1 || dnum > n_q) fail(CKKS_EINVAL, "need n_q >= 2, n_p >= 1, 1 <= dnum <= n_q");
+        auto C = std::make_unique<ckks_ctx>();
+        C->device = device;
+        C->log_n = log_n;
+        C->N = 1u << log_n;
+        C->L = n_q;
+        C->K = n_p;
+        C->dnum = dnum;
+        C->alpha = (n_q + dnum - 1) / dnum;
+        C->beta_max = (n_q + C->alpha - 1) / C->alpha;
+        if (C->alpha > 64 || C->K > 63) fail(CKKS_EINVAL, "alpha and k must be at most 64 and 63");
+        for (u32 i = 0; i < n_q; i++) C->mods.push_back(q[i]);
+        for (u32 i = 0; i < n_p; i++) C->mods.push_back(p[i]);
+        const u64 two_n = 2ull * C->N;
+        for (size_t i = 0; i < C->mods.size(); i++) {
+            const u64 m = C->mods[i];
+            if (m >= (1ull << 60) || m % two_n != 1 || !is_prime_h(m))
+                fail(CKKS_EINVAL, "modulus " + std::to_string(i) + " is not a prime = 1 mod 2N below 2^60");
+            for (size_t j = 0; j < i; j++)
+                if (C->mods[j] == m) fail(CKKS_EINVAL, "moduli must be distinct");
+        }
+        CK(cudaSetDevice(device));
+        cudaMemPool_t pool;
+        CK(cudaDeviceGetDefaultMemPool(&pool, device));
+        uint64_t thr = UINT64_MAX;
+        CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        const u32 nm = (u32)C->mods.size(), N = C->N;
+        std::vector<ModC> mc(nm);
+        std::vector<u64> psi((size_t)nm * N), psh((size_t)nm * N), ipsi((size_t)nm * N), ish((size_t)nm * N);
+        std::vector<u64> lift(nm, 0), lsh(nm, 0);
+        for (u32 i = 0; i < nm; i++) {
+            const u64 m = C->mods[i];
+            mc[i] = modc_h(m);
+            // psi = x^((m-1)/2N) for the smallest x >= 2 with psi^N = -1
+            u64 w = 0;
+            for (u64 x = 2;; x++) {
+                w = powmod_h(x, (m - 1) / two_n, m);
+                if (powmod_h(w, N, m) == m - 1) break;
+            }
+            const u64 wi = invmod_h(w, m);
+            std::vector<u64> pw(N), ipw(N);
+            pw[0] = ipw[0] = 1;
+            for (u32 k = 1; k < N; k++) pw[k] = mulmod_h(pw[k - 1], w, m), ipw[k] = mulmod_h(ipw[k - 1], wi, m);
+            for (u32 k = 0; k < N; k++) {
+                const u32 e = brv_h(k, log_n);
+                psi[(size_t)i * N + k] = pw[e];
+                psh[(size_t)i * N + k] = shoup_h(pw[e], m);
+                ipsi[(size_t)i * N + k] = ipw[e];
+                ish[(size_t)i * N + k] = shoup_h(ipw[e], m);
+            }
+            if (i < n_q) {
+                u64 P = 1;
+                for (u32 k = 0; k < n_p; k++) P = mulmod_h(P, p[k] % m, m);
+                lift[i] = P;
+                lsh[i] = shoup_h(P, m);
+            }
+        }
+        C->d_mods.p = C->dalloc((nm * sizeof(ModC) + 7) / 8);
+        CK(cudaMemcpy(C->d_mods.p, mc.data(), nm * sizeof(ModC), cudaMemcpyHostToDevice));
+        C->d_psi.p = C->upload(psi);
+        C->d_psi_sh.p = C->upload(psh);
+        C->d_ipsi.p = C->upload(ipsi);
+        C->d_ipsi_sh.p = C->upload(ish);
+        C->d_lift.p = C->upload(lift);
+        C->d_lift_sh.p = C->upload(lsh);
+        C->T = NttTables{(const ModC*)C->d_mods.p, C->d_psi.p, C->d_psi_sh.p, C->d_ipsi.p, C->d_ipsi_sh.p, log_n};
+        *out = C.release();
+    });
+}
+
+ckks_status ckks_ctx_destroy(ckks_ctx* ctx) {
+    return guarded([&] {
+        if (!ctx) return;
+        cudaSetDevice(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto& kv : ctx->keys) cudaFree(kv.second);
+        for (auto& kv : ctx->levels) {
+            cudaFree(kv.second.dec_tab);
+            cudaFree(kv.second.md_tab);
+            cudaFree(kv.second.mdr_tab);
+            cudaFree(kv.second.rs_tab);
+        }
+        for (DevBuf* b : {&ctx->d_mods, &ctx->d_psi, &ctx->d_psi_sh, &ctx->d_ipsi, &ctx->d_ipsi_sh, &ctx->d_lift,
+                          &ctx->d_lift_sh})
+            cudaFree(b->p);
+        delete ctx;
+    });
+}
+
+static void put_key(ckks_ctx* ctx, int32_t r, const uint64_t* src, size_t n_words, cudaMemcpyKind kind,
+                    cudaStream_t st) {
+    if (!ctx || !src) fail(CKKS_EINVAL, "null argument");
+    if (n_words != ctx->key_words()) fail(CKKS_EINVAL, "key size must be beta_max*2*(L+k)*N words");
+    CK(cudaSetDevice(ctx->device));
+    const u32 rk = ctx->rotkey(r);
+    u64* d;
+    auto it = ctx->keys.find(rk);
+    if (it != ctx->keys.end()) d = it->second;
+    else d = ctx->dalloc(n_words);
+    ctx->keys[rk] = d;
+    if (kind == cudaMemcpyHostToDevice) CK(cudaMemcpy(d, src, n_words * 8, kind));
+    else CK(cudaMemcpyAsync(d, src, n_words * 8, kind, st));
+}
+
+ckks_status ckks_upload_rotation_key(ckks_ctx* ctx, int32_t r, const uint64_t* host, size_t n_words) {
+    return guarded([&] { put_key(ctx, r, host, n_words, cudaMemcpyHostToDevice, 0); });
+}
+
+ckks_status ckks_upload_rotation_key_device(ckks_ctx* ctx, int32_t r, const uint64_t* dev, size_t n_words,
+                                            void* stream) {
+    return guarded([&] { put_key(ctx, r, dev, n_words, cudaMemcpyDeviceToDevice, (cudaStream_t)stream); });
+}
+
+int ckks_has_rotation_key(const ckks_ctx* ctx, int32_t r) {
+    return ctx && ctx->keys.count(ctx->rotkey(r)) ? 1 : 0;
+}
+
+static void put_diags(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t offset0, int32_t stride,
+                      uint32_t level, const uint64_t* host, size_t n_words, cudaMemcpyKind kind, cudaStream_t st) {
+        if (!ctx || !out || !host) fail(CKKS_EINVAL, "null argument");
+        *out = nullptr;
+        if (offset0 != 0) fail(CKKS_EINVAL, "offset0 must be 0");
+        if (stride < 1 || n_diag < 1) fail(CKKS_EINVAL, "need n_diag >= 1 and stride >= 1");
+        if ((u64)stride * (n_diag - 1) >= ctx->slots()) fail(CKKS_EINVAL, "offsets exceed N/2");
+        if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        if (n_words != (size_t)n_diag * (level + ctx->K) * ctx->N) fail(CKKS_EINVAL, "size mismatch");
+        CK(cudaSetDevice(ctx->device));
+        auto f = std::make_unique<ckks_diags>();
+        f->ctx = ctx;
+        f->n_diag = n_diag;
+        f->level = level;
+        f->offset0 = offset0;
+        f->stride = stride;
+        f->d = ctx->dalloc(n_words);
+        if (kind == cudaMemcpyHostToDevice) CK(cudaMemcpy(f->d, host, n_words * 8, kind));
+        else CK(cudaMemcpyAsync(f->d, host, n_words * 8, kind, st));
+        *out = f.release();
+}
+
+ckks_status ckks_upload_diagonals(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t offset0, int32_t stride,
+                                  uint32_t level, const uint64_t* host, size_t n_words) {
+    return guarded([&] {
+        put_diags(ctx, out, n_diag, offset0, stride, level, host, n_words, cudaMemcpyHostToDevice, 0);
+    });
+}
+
+ckks_status ckks_upload_diagonals_device(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t offset0,
+                                         int32_t stride, uint32_t level, const uint64_t* dev, size_t n_words,
+                                         void* stream) {
+    return guarded([&] {
+        put_diags(ctx, out, n_diag, offset0, stride, level, dev, n_words, cudaMemcpyDeviceToDevice,
+                  (cudaStream_t)stream);
+    });
+}
+
+ckks_status ckks_free_diags(ckks_diags* f) {
+    return guarded([&] {
+        if (!f) return;
+        cudaSetDevice(f->ctx->device);
+        f->ctx->dfree(f->d, (size_t)f->n_diag * (f->level + f->ctx->K) * f->ctx->N);
+        delete f;
+    });
+}
+
+ckks_status ckks_ct_create(ckks_ctx* ctx, ckks_ct** out, uint32_t level) {
+    return guarded([&] {
+        if (!ctx || !out) fail(CKKS_EINVAL, "null argument");
+        if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        CK(cudaSetDevice(ctx->device));
+        *out = new ckks_ct{ctx, level, ctx->dalloc(2ull * level * ctx->N), true};
+    });
+}
+
+ckks_status ckks_ct_upload(ckks_ctx* ctx, ckks_ct** out, uint32_t level, const uint64_t* host) {
+    ckks_status st = ckks_ct_create(ctx, out, level);
+    if (st != CKKS_OK) return st;
+    return guarded([&] {
+        if (!host) fail(CKKS_EINVAL, "null host buffer");
+        CK(cudaMemcpy((*out)->d, host, 2ull * level * ctx->N * 8, cudaMemcpyHostToDevice));
+    });
+}
+
+ckks_status ckks_ct_wrap_device(ckks_ctx* ctx, ckks_ct** out, uint32_t level, uint64_t* dev_ptr) {
+    return guarded([&] {
+        if (!ctx || !out || !dev_ptr) fail(CKKS_EINVAL, "null argument");
+        if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        *out = new ckks_ct{ctx, level, dev_ptr, false};
+    });
+}
+
+ckks_status ckks_ct_h2d_async(ckks_ct* ct, const uint64_t* host, size_t n_words, void* stream) {
+    return guarded([&] {
+        if (!ct || !host) fail(CKKS_EINVAL, "null argument");
+        if (n_words != 2ull * ct->level * ct->ctx->N) fail(CKKS_EINVAL, "size mismatch");
+        CK(cudaMemcpyAsync(ct->d, host, n_words * 8, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    });
+}
+
+ckks_status ckks_ct_d2h_async(const ckks_ct* ct, uint64_t* host, size_t n_words, void* stream) {
+    return guarded([&] {
+        if (!ct || !host) fail(CKKS_EINVAL, "null argument");
+        if (n_words != 2ull * ct->level * ct->ctx->N) fail(CKKS_EINVAL, "size mismatch");
+        CK(cudaMemcpyAsync(host, ct->d, n_words * 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    });
+}
+
+ckks_status ckks_ct_download(const ckks_ct* ct, uint64_t* host, size_t n_words) {
+    return guarded([&] {
+        if (!ct || !host) fail(CKKS_EINVAL, "null argument");
+        if (n_words != 2ull * ct->level * ct->ctx->N) fail(CKKS_EINVAL, "size mismatch");
+        CK(cudaSetDevice(ct->ctx->device));
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(host, ct->d, n_words * 8, cudaMemcpyDeviceToHost));
+    });
+}
+
+uint32_t ckks_ct_level(const ckks_ct* ct) { return ct ? ct->level : 0; }
+uint64_t* ckks_ct_device_ptr(const ckks_ct* ct) { return ct ? ct->d : nullptr; }
+
+ckks_status ckks_free_ct(ckks_ct* ct) {
+    return guarded([&] {
+        if (!ct) return;
+        if (ct->owned) {
+            cudaSetDevice(ct->ctx->device);
+            ct->ctx->dfree(ct->d, 2ull * ct->level * ct->ctx->N);
+        }
+        delete ct;
+    });
+}
+
+int32_t lt_required_rotations(const ckks_ctx* ctx, lt_algo algo, const lt_split* split, uint32_t n_diag,
+                              int32_t stride, int32_t* rot_out, uint32_t cap) {
+    if (!ctx) return -1;
+    lt_split sp = split ? *split : lt_split{0, 0, 0};
+    if (algo == LT_DIAG) sp = lt_split{1, n_diag, 1};
+    if (sp.n3 == 0 && algo != LT_TH_BSGS) sp.n3 = 1;
+    try {
+        validate_split(algo, n_diag, sp);
+    } catch (const Fail&) {
+        return -1;
+    }
+    std::vector<u32> rs;
+    for (int64_t r : rotations(algo, sp, n_diag)) rs.push_back(ctx->rotkey(r * stride));
+    std::sort(rs.begin(), rs.end());
+    rs.erase(std::unique(rs.begin(), rs.end()), rs.end());
+    u32 n = 0;
+    for (u32 r : rs)
+        if (n < cap && rot_out) rot_out[n++] = (int32_t)r;
+        else n++;
+    return (int32_t)std::min<u32>(n, cap);
+}
+
+ckks_status lt_choose_split(ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out) {
+    return guarded([&] {
+        if (!ctx || !out) fail(CKKS_EINVAL, "null argument");
+        *out = choose_split(ctx, algo, level, n_diag);
+        if (out->n1 == 0) fail(CKKS_EINVAL, "no admissible split");
+    });
+}
+
+static void lt_eval_impl(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_algo algo, const lt_split* split,
+                         ckks_ct* out, cudaStream_t st, lt_split* chosen) {
+    if (!ctx || !in || !f || !out) fail(CKKS_EINVAL, "null argument");
+    if (in->ctx != ctx || f->ctx != ctx || out->ctx != ctx) fail(CKKS_EINVAL, "objects of another context");
+    const u32 level = in->level;
+    if (level < 2) fail(CKKS_EINVAL, "input level must be >= 2");
+    if (level > f->level) fail(CKKS_EINVAL, "diagonals encoded below the ciphertext level");
+    if (out->level != level - 1) fail(CKKS_EINVAL, "output level must be input level - 1");
+    if (out->d == in->d) fail(CKKS_EINVAL, "output must not alias input");
+    const u32 D = f->n_diag;
+    lt_split sp = (split && (split->n1 || split->n2 || split->n3)) ? *split : choose_split(ctx, algo, level, D);
+    if (algo == LT_DIAG) sp = lt_split{1, D, 1};
+    if (algo != LT_TH_BSGS && sp.n3 == 0) sp.n3 = 1;
+    validate_split(algo, D, sp);
+    for (int64_t r : rotations(algo, sp, D)) key_of(ctx, r * f->stride);
+    if (chosen) *chosen = sp;
+    CK(cudaSetDevice(ctx->device));
+    const size_t lw = (size_t)level * ctx->N;
+    LtIO io{in->d, in->d + lw, out->d, out->d + (size_t)(level - 1) * ctx->N};
+    switch (algo) {
+        case LT_TH_BSGS: sched_th(ctx, level, io, f, sp.n1, sp.n2, sp.n3, st); break;
+        case LT_DH_BSGS: sched_th(ctx, level, io, f, sp.n1, 1, sp.n2, st); break;
+        case LT_DIAG: sched_th(ctx, level, io, f, 1, D, 1, st); break;
+        case LT_BSGS: sched_bsgs(ctx, level, io, f, sp.n1, sp.n2, st); break;
+    }
+    CK(cudaGetLastError());
+}
+
+ckks_status lt_eval(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_algo algo, const lt_split* split,
+                    ckks_ct* out, void* stream, lt_split* chosen) {
+    return guarded([&] { lt_eval_impl(ctx, in, f, algo, split, out, (cudaStream_t)stream, chosen); });
+}
+
+ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* in, const ckks_diags* const* f,
+                          const lt_algo* algos, const lt_split* splits, ckks_ct* const* out, void* stream) {
+    return guarded([&] {
+        if (!ctx || (count && (!in || !f || !out))) fail(CKKS_EINVAL, "null argument");
+        for (u32 i = 0; i < count; i++)
+            lt_eval_impl(ctx, in[i], f[i], algos ? algos[i] : LT_TH_BSGS, splits ? &splits[i] : nullptr, out[i],
+                         (cudaStream_t)stream, nullptr);
+    });
+}
+
+// ------------------------------------------------------------------ steps
+ckks_status ckks_poly_ntt(ckks_ctx* ctx, uint64_t* poly, uint32_t level, int ext, int inverse, void* stream) {
+    return guarded([&] {
+        if (!ctx || !poly) fail(CKKS_EINVAL, "null argument");
+        if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        CK(cudaSetDevice(ctx->device));
+        const u32 nl = level + (ext ? ctx->K : 0), N = ctx->N;
+        if (inverse) {
+            std::vector<InvJob> j(nl);
+            for (u32 t = 0; t < nl; t++) {
+                const u32 g = ctx->gmod(level, t);
+                const u64 m = ctx->mods[g], ninv = invmod_h(N % m, m);
+                j[t] = InvJob{poly + (size_t)t * N, poly + (size_t)t * N, poly + (size_t)t * N, ninv, shoup_h(ninv, m), g,
+                              0};
+            }
+            launch_inv_ntt(ctx->T, j.data(), (int)nl, (cudaStream_t)stream);
+        } else {
+            std::vector<FwdJob> j(nl);
+            for (u32 t = 0; t < nl; t++)
+                j[t] = FwdJob{poly + (size_t)t * N, poly + (size_t)t * N, nullptr, nullptr, nullptr, 0, 0,
+                              ctx->gmod(level, t), 0};
+            launch_fwd_ntt(ctx->T, j.data(), (int)nl, (cudaStream_t)stream);
+        }
+        CK(cudaGetLastError());
+    });
+}
+
+ckks_status ckks_decompose(ckks_ctx* ctx, uint32_t level, const uint64_t* c, int32_t rot, uint64_t* digits,
+                           void* stream) {
+    return guarded([&] {
+        if (!ctx || !c || !digits) fail(CKKS_EINVAL, "null argument");
+        if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        CK(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        Arena ar(st, ctx->N);
+        u64* Y = ar.limbs(level);
+        op_decompose(ctx, level, c, ctx->rotkey(rot) ? ctx->galois(rot) : 0, digits, Y, st);
+        CK(cudaGetLastError());
+    });
+}
+
+ckks_status ckks_ks_inner(ckks_ctx* ctx, uint32_t level, const uint64_t* digits, int32_t key_rot, int32_t rot,
+                          const uint64_t* x0, int lift_x0, uint64_t* out0, uint64_t* out1, int accumulate,
+                          void* stream) {
+    return guarded([&] {
+        if (!ctx || !digits || !out0 || !out1) fail(CKKS_EINVAL, "null argument");
+        if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        CK(cudaSetDevice(ctx->device));
+        op_ks_inner(ctx, level, digits, key_of(ctx, key_rot), ctx->rotkey(rot) ? ctx->galois(rot) : 0, x0,
+                    lift_x0 ? 2 : 1, out0, out1, accumulate, (cudaStream_t)stream);
+        CK(cudaGetLastError());
+    });
+}
+
+ckks_status ckks_moddown(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out, void* stream) {
+    return guarded([&] {
+        if (!ctx || !x || !out) fail(CKKS_EINVAL, "null argument");
+        if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        if (x == out) fail(CKKS_EINVAL, "ModDown cannot run in place");
+        CK(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        Arena ar(st, ctx->N);
+        op_moddown(ctx, level, x, out, ar.limbs(ctx->K), st);
+        CK(cudaGetLastError());
+    });
+}
+
+ckks_status ckks_moddown_rescale(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out, void* stream) {
+    return guarded([&] {
+        if (!ctx || !x || !out) fail(CKKS_EINVAL, "null argument");
+        if (level < 2 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        CK(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        Arena ar(st, ctx->N);
+        op_moddown_rescale(ctx, level, x, out, ar.limbs(ctx->K + 1), st);
+        CK(cudaGetLastError());
+    });
+}
+
+ckks_status ckks_rescale(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out, void* stream) {
+    return guarded([&] {
+        if (!ctx || !x || !out) fail(CKKS_EINVAL, "null argument");
+        if (level < 2 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        CK(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        Arena ar(st, ctx->N);
+        op_rescale(ctx, level, x, out, ar.limbs(1), st);
+        CK(cudaGetLastError());
+    });
+}
+
+ckks_status ckks_automorphism(ckks_ctx* ctx, uint32_t n_limbs, const uint64_t* in, int32_t rot, uint64_t* out,
+                              void* stream) {
+    return guarded([&] {
+        if (!ctx || !in || !out) fail(CKKS_EINVAL, "null argument");
+        if (in == out) fail(CKKS_EINVAL, "automorphism cannot run in place");
+        CK(cudaSetDevice(ctx->device));
+        if (ctx->rotkey(rot) == 0)
+            CK(cudaMemcpyAsync(out, in, (size_t)n_limbs * ctx->N * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+        else launch_automorphism(in, out, n_limbs, ctx->galois(rot), ctx->log_n, (cudaStream_t)stream);
+        CK(cudaGetLastError());
+    });
+}
+
+}  // extern "C"

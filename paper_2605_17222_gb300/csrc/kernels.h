@@ -1,0 +1,125 @@
+// Kernel launch interface shared by the .cu files of the library (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "modarith.cuh"
+
+namespace ckks {
+
+// Per-context device tables every NTT kernel reads.
+struct NttTables {
+    const ModC* mods;     // [n_mod] {q, mu}
+    const u64* psi;       // [n_mod][N]  psi^brv(i)
+    const u64* psi_sh;    // Shoup companions
+    const u64* ipsi;      // [n_mod][N]  psi^-brv(i)
+    const u64* ipsi_sh;
+    u32 log_n;
+};
+
+// One limb of a forward NTT.
+//   pass 1 load : nsrc == 0 -> src[x];
+//                 nsrc  > 0 -> sum_j src[j*N + x] * bcst[j] mod q   (basis conversion, Eq. 3)
+//   pass 2 store: subout == nullptr -> dst[x] = X;
+//                 otherwise subout[x] = (subx[x] - X) * c mod q        (ModDown tail, Eq. 4)
+// Pass 1 writes dst; pass 2 runs in place on dst.
+struct FwdJob {
+    const u64* src;
+    u64* dst;
+    const u64* bcst;
+    const u64* subx;
+    u64* subout;
+    u64 c, c_sh;
+    u32 mod;
+    u32 nsrc;
+};
+
+// One limb of an inverse NTT: pass A reads src (gathered through x -> x^gal
+// when gal != 0) and writes tmp; pass B reads tmp and writes dst scaled by c
+// (c includes N^-1).  tmp may alias dst; src may alias tmp only when gal == 0.
+struct InvJob {
+    const u64* src;
+    u64* tmp;
+    u64* dst;
+    u64 c, c_sh;
+    u32 mod;
+    u32 gal;
+};
+
+void launch_fwd_ntt(const NttTables& T, const FwdJob* jobs, int njobs, cudaStream_t st);
+void launch_inv_ntt(const NttTables& T, const InvJob* jobs, int njobs, cudaStream_t st);
+
+// out[l][s] = in[l][src_g(s)] for n_limbs limbs (NTT-domain automorphism, Eq. 7).
+void launch_automorphism(const u64* in, u64* out, u32 n_limbs, u32 gal, u32 log_n, cudaStream_t st);
+
+// out[s] = (acc ? out[s] : 0) + a[src_g(s)] + b[s] mod q_l, per limb (b may be null).
+struct AddJob {
+    const u64* a;
+    const u64* b;
+    u64* out;
+    u32 mod;
+    u32 pad;
+};
+void launch_add_gather(const ModC* mods, const AddJob* jobs, int njobs, u32 gal, int accumulate, u32 log_n,
+                       cudaStream_t st);
+
+// Switching-key inner product with hoisted automorphism (K4).
+struct KsArgs {
+    const u64* digits;      // [beta][ext][N]
+    const u64* key;         // [beta_max][2][L+k][N]
+    const u64* x0;          // null, ext poly, or Q poly to lift
+    u64* out0;
+    u64* out1;
+    const ModC* mods;       // context moduli (index = global modulus id)
+    const u64* lift_c;      // [L+k] [P]_{q_j} (0 for P moduli) and Shoup companions
+    const u64* lift_sh;
+    u32 level, ext, L, beta, beta_max, gal, x0_mode, accumulate, log_n;
+};
+void launch_ks_inner(const KsArgs& a, cudaStream_t st);
+
+// Multi-output plaintext-diagonal multiply-accumulate with the middle
+// (hoisted) key-switch layer fused in (K6).  See ks.cu.
+constexpr int DM_MAX_N1 = 64;
+constexpr int DM_MAX_N2 = 1024;
+constexpr int DM_MAX_K3 = 8;   // giant indices per thread (grid.z covers the rest)
+constexpr int DM_MAX_N3 = 64;
+struct DiagMacArgs {
+    const ModC* mods;
+    const u64* lift_c;
+    const u64* lift_sh;
+    const u64* diags;       // [n_diag][diag_level + k][N]
+    const u64* A[DM_MAX_N1];
+    const u64* B[DM_MAX_N1];
+    const u64* Dg[DM_MAX_N1];        // digits per baby index (middle layer), [beta][ext][N]
+    const u64* keys[DM_MAX_N2];      // middle-layer keys, index j (j >= 1)
+    u32 gal_mid[DM_MAX_N2];          // x -> x^gal for rotation n1*j*stride
+    u64* U0[DM_MAX_N3];
+    u64* U1[DM_MAX_N3];
+    u32 gal_diag[DM_MAX_N3];         // rotation -(n1*n2*k*stride), 0 = none
+    u32 level, ext, L, k_p, beta, log_n;
+    u32 n1, n2, n3, lift0, diag_level;
+};
+void launch_diag_mac(const DiagMacArgs& a, cudaStream_t st);
+
+uint64_t launches();
+void count_launch(int n = 1);
+
+// Kernel classes for live timing (ckks_profile_*).
+enum KClass { K_DIAG_MAC = 0, K_KS_INNER, K_FWD_COLS, K_FWD_ROWS, K_INV_ROWS, K_INV_COLS, K_AUTO, K_ADD, K_NCLASS };
+extern const char* const kclass_names[K_NCLASS];
+bool prof_on(int cls);
+// Brackets one launch with events when its class is enabled.
+struct ProfScope {
+    int cls;
+    cudaStream_t st;
+    void* ev;
+    ProfScope(int c, cudaStream_t s);
+    ~ProfScope();
+};
+int prof_class(const char* name);
+void prof_enable(int cls, bool on);
+bool prof_read(int cls, double* ms, uint64_t* n);
+void prof_reset();
+
+}  // namespace ckks

@@ -257,3 +257,16 @@ def diagonal_values(seed: int, stream, n_diag: int, n_slots: int) -> np.ndarray:
     through its nonzero diagonals and never materialised.
     """
     return uniform_real(seed, stream, n_diag * n_slots).reshape(n_diag, n_slots)
+
+
+def uniform_mod_device(seed: int, stream, moduli, n: int, count: int = 1, device="cuda"):
+    """[count][len(moduli)][n] int64 device tensor, row i uniform in
+    [0, moduli[i]) (torch's seeded generator on the device).  Used for
+    throughput runs whose values need only the right shape and range."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed((seed * 0x9E3779B1 + stream_id(stream)) % (1 << 63))
+    out = torch.empty((count, len(moduli), n), dtype=torch.int64, device=device)
+    for i, q in enumerate(moduli):
+        out[:, i].random_(0, int(q), generator=g)
+    return out

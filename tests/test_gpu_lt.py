@@ -1,0 +1,134 @@
+"""End-to-end parity of lt_eval with the CPU oracle: every algorithm, several
+splits, strided offsets, lower levels, the library's own split choice, and
+the full-size workload (N = 2^16, 24 Q limbs, 4 special primes, dnum 6,
+256 consecutive diagonals).  Output residues must be identical bit for bit;
+the decrypted result must match the FP64 product within 1e-5 (64 diagonals)
+or 1e-4 (256 diagonals)."""
+import numpy as np
+import pytest
+
+from oracle.workload import make_problem
+from paper_2605_17222_gb300 import binding
+
+from gpu_common import TOY_SPLITS, assert_same, ensure_keys, gpu_context, oracle_lt, upload_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def max_err(pb, ct):
+    y = pb.decrypt((ct[0], ct[1]))
+    e = y - pb.expected()
+    return float(np.max(np.maximum(np.abs(e.real), np.abs(e.imag))))
+
+
+@pytest.fixture(scope="module")
+def toy():
+    pb = make_problem("toy", 0, 64)
+    for algo, split in TOY_SPLITS.items():
+        ensure_keys(pb, algo, split)
+    for split in [(2, 4, 8), (1, 8, 8), (8, 8, 1), (1, 64, 1), (16, 2, 2)]:
+        ensure_keys(pb, "th", split)
+    ensure_keys(pb, "dh", (4, 16))
+    g = gpu_context("toy")
+    f = upload_problem(g, pb)
+    return pb, g, f
+
+
+@pytest.mark.parametrize("algo", list(TOY_SPLITS))
+def test_toy_all_algorithms(toy, algo):
+    pb, g, f = toy
+    split = TOY_SPLITS[algo]
+    want = oracle_lt(pb, algo, split)
+    out, chosen = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, algo, split)
+    got = out.numpy()
+    assert_same(got, want, f"toy {algo}")
+    assert max_err(pb, got) <= 1e-5
+
+
+@pytest.mark.parametrize("algo,split", [("th", (2, 4, 8)), ("th", (1, 8, 8)), ("th", (8, 8, 1)),
+                                        ("th", (16, 2, 2)), ("dh", (4, 16))])
+def test_toy_other_splits(toy, algo, split):
+    pb, g, f = toy
+    out, _ = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, algo, split)
+    assert_same(out.numpy(), oracle_lt(pb, algo, split), f"toy {algo} {split}")
+
+
+def test_toy_special_splits_match_other_algorithms(toy):
+    """TH(1, 8, 8) == DH(8, 8) and TH(1, 64, 1) == diagonal method, on the GPU too."""
+    pb, g, f = toy
+    ct = g.ct_from_host(np.stack(pb.ct))
+    a, _ = g.lt_eval(ct, f, "th", (1, 8, 8))
+    b, _ = g.lt_eval(ct, f, "dh", (8, 8))
+    assert_same(a.numpy(), b.numpy(), "TH(1,8,8) vs DH(8,8)")
+    c, _ = g.lt_eval(ct, f, "th", (1, 64, 1))
+    d, _ = g.lt_eval(ct, f, "diag")
+    assert_same(c.numpy(), d.numpy(), "TH(1,64,1) vs diagonal")
+
+
+def test_toy_strided_lower_level():
+    """Offsets strided by 4 (a CoeffToSlot-like stage) at level 3, and the
+    minimum level 2."""
+    for level, stride, D, split in [(3, 4, 16, (2, 2, 4)), (2, 1, 8, (2, 2, 2))]:
+        pb = make_problem("toy", 3, D, level=level, stride=stride)
+        ensure_keys(pb, "th", split)
+        g = gpu_context("toy")
+        f = upload_problem(g, pb, stride=stride)
+        out, _ = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, "th", split)
+        got = out.numpy()
+        assert_same(got, oracle_lt(pb, "th", split), f"strided level {level}")
+        assert max_err(pb, got) <= 1e-5
+
+
+def test_toy_autotuned_split(toy):
+    pb, g, f = toy
+    split = g.choose_split("th", pb.level, pb.D)
+    ensure_keys(pb, "th", split)
+    upload_problem(g, pb)
+    out, chosen = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, "th")
+    assert chosen == split
+    assert_same(out.numpy(), oracle_lt(pb, "th", split), f"auto {split}")
+
+
+def test_missing_key_is_reported(toy):
+    pb, g, f = toy
+    with pytest.raises(binding.CkksError) as e:
+        g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, "th", (2, 2, 16))
+    assert e.value.status == 3
+
+
+def test_bad_split_is_rejected(toy):
+    pb, g, f = toy
+    with pytest.raises(binding.CkksError) as e:
+        g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, "th", (3, 3, 3))
+    assert e.value.status == 1
+
+
+# ---------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def full():
+    """N = 2^16, Q = 55b + 23x40b, P = 4x60b, dnum 6, D = 256 consecutive, seed 1."""
+    pb = make_problem("n16", 1, 256)
+    g = gpu_context("n16")
+    f = upload_problem(g, pb)
+    return pb, g, f
+
+
+@pytest.mark.parametrize("algo,split", [("th", (4, 8, 8)), ("dh", (16, 16)), ("bsgs", (16, 16))])
+def test_full_size_bit_exact(full, algo, split):
+    pb, g, f = full
+    ensure_keys(pb, algo, split)
+    upload_problem(g, pb)
+    out, _ = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, algo, split)
+    got = out.numpy()
+    assert_same(got, oracle_lt(pb, algo, split), f"full {algo} {split}")
+    assert max_err(pb, got) <= 1e-4
+
+
+def test_full_size_autotuned_th(full):
+    pb, g, f = full
+    split = g.choose_split("th", pb.level, pb.D)
+    ensure_keys(pb, "th", split)
+    upload_problem(g, pb)
+    out, chosen = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, "th")
+    assert chosen == split
+    assert_same(out.numpy(), oracle_lt(pb, "th", split), f"full auto {split}")
