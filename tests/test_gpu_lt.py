@@ -90,7 +90,11 @@ def test_toy_autotuned_split(toy):
 
 
 def test_missing_key_is_reported(toy):
-    pb, g, f = toy
+    """A context holding only some keys refuses the LT with CKKS_ENOKEY before any launch."""
+    pb, _, _ = toy
+    g = gpu_context("toy")
+    g.upload_rotation_key(1, pb.keys[1])
+    f = g.upload_diagonals(pb.diags)
     with pytest.raises(binding.CkksError) as e:
         g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, "th", (2, 2, 16))
     assert e.value.status == 3
