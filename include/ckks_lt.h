@@ -84,7 +84,7 @@ typedef struct {
 /* ------------------------------------------------------------------ context */
 
 /* Create a context on CUDA device `device` for ring degree N = 2^log_n
- * (10 <= log_n <= 17), Q chain q[0..n_q-1], special primes p[0..n_p-1]
+ * (12 <= log_n <= 16), Q chain q[0..n_q-1], special primes p[0..n_p-1]
  * (n_p >= 1) and dnum digits at the top level (Sec. II-A, Fig. 1).
  * Computes and uploads every constant (twiddles, basis-conversion tables).
  * EINVAL on a modulus that is not an NTT-friendly prime below 2^60. */

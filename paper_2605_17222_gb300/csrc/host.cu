@@ -132,7 +132,7 @@ struct ckks_ctx {
     int device = 0;
     u32 log_n = 0, N = 0, L = 0, K = 0, dnum = 0, alpha = 0, beta_max = 0;
     std::vector<u64> mods;  // q_0..q_{L-1}, p_0..p_{K-1}
-    DevBuf d_mods, d_psi, d_psi_sh, d_ipsi, d_ipsi_sh, d_lift, d_lift_sh;
+    DevBuf d_mods, d_psi, d_ipsi, d_lift, d_lift_sh;
     NttTables T{};
     std::map<u32, LevelConsts> levels;
     std::map<u32, u64*> keys;  // rotation (mod N/2) -> [beta_max][2][L+K][N]
@@ -662,7 +662,7 @@ ckks_status ckks_ctx_create(ckks_ctx** out, uint32_t log_n, const uint64_t* q, u
     return guarded([&] {
         if (!out || !q || !p) fail(CKKS_EINVAL, "null argument");
         *out = nullptr;
-        if (log_n < 10 || log_n > 17) fail(CKKS_EINVAL, "log_n must be in [10, 17]");
+        if (log_n < 12 || log_n > 16) fail(CKKS_EINVAL, "log_n must be in [12, 16]");
         if (n_q < 2 || n_p < 1 || dnum < 1 || dnum > n_q) fail(CKKS_EINVAL, "need n_q >= 2, n_p >= 1, 1 <= dnum <= n_q");
         auto C = std::make_unique<ckks_ctx>();
         C->device = device;
@@ -691,7 +691,7 @@ ckks_status ckks_ctx_create(ckks_ctx** out, uint32_t log_n, const uint64_t* q, u
         CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
         const u32 nm = (u32)C->mods.size(), N = C->N;
         std::vector<ModC> mc(nm);
-        std::vector<u64> psi((size_t)nm * N), psh((size_t)nm * N), ipsi((size_t)nm * N), ish((size_t)nm * N);
+        std::vector<u64> psi((size_t)nm * N * 2), ipsi((size_t)nm * N * 2);  // (w, Shoup(w)) pairs
         std::vector<u64> lift(nm, 0), lsh(nm, 0);
         for (u32 i = 0; i < nm; i++) {
             const u64 m = C->mods[i];
@@ -708,10 +708,10 @@ ckks_status ckks_ctx_create(ckks_ctx** out, uint32_t log_n, const uint64_t* q, u
             for (u32 k = 1; k < N; k++) pw[k] = mulmod_h(pw[k - 1], w, m), ipw[k] = mulmod_h(ipw[k - 1], wi, m);
             for (u32 k = 0; k < N; k++) {
                 const u32 e = brv_h(k, log_n);
-                psi[(size_t)i * N + k] = pw[e];
-                psh[(size_t)i * N + k] = shoup_h(pw[e], m);
-                ipsi[(size_t)i * N + k] = ipw[e];
-                ish[(size_t)i * N + k] = shoup_h(ipw[e], m);
+                psi[2 * ((size_t)i * N + k)] = pw[e];
+                psi[2 * ((size_t)i * N + k) + 1] = shoup_h(pw[e], m);
+                ipsi[2 * ((size_t)i * N + k)] = ipw[e];
+                ipsi[2 * ((size_t)i * N + k) + 1] = shoup_h(ipw[e], m);
             }
             if (i < n_q) {
                 u64 P = 1;
@@ -723,12 +723,11 @@ ckks_status ckks_ctx_create(ckks_ctx** out, uint32_t log_n, const uint64_t* q, u
         C->d_mods.p = C->dalloc((nm * sizeof(ModC) + 7) / 8);
         CK(cudaMemcpy(C->d_mods.p, mc.data(), nm * sizeof(ModC), cudaMemcpyHostToDevice));
         C->d_psi.p = C->upload(psi);
-        C->d_psi_sh.p = C->upload(psh);
         C->d_ipsi.p = C->upload(ipsi);
-        C->d_ipsi_sh.p = C->upload(ish);
         C->d_lift.p = C->upload(lift);
         C->d_lift_sh.p = C->upload(lsh);
-        C->T = NttTables{(const ModC*)C->d_mods.p, C->d_psi.p, C->d_psi_sh.p, C->d_ipsi.p, C->d_ipsi_sh.p, log_n};
+        C->T = NttTables{(const ModC*)C->d_mods.p, (const ulonglong2*)C->d_psi.p, (const ulonglong2*)C->d_ipsi.p,
+                         log_n};
         *out = C.release();
     });
 }
@@ -745,8 +744,7 @@ ckks_status ckks_ctx_destroy(ckks_ctx* ctx) {
             cudaFree(kv.second.mdr_tab);
             cudaFree(kv.second.rs_tab);
         }
-        for (DevBuf* b : {&ctx->d_mods, &ctx->d_psi, &ctx->d_psi_sh, &ctx->d_ipsi, &ctx->d_ipsi_sh, &ctx->d_lift,
-                          &ctx->d_lift_sh})
+        for (DevBuf* b : {&ctx->d_mods, &ctx->d_psi, &ctx->d_ipsi, &ctx->d_lift, &ctx->d_lift_sh})
             cudaFree(b->p);
         delete ctx;
     });

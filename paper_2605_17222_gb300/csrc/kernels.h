@@ -10,11 +10,9 @@ namespace ckks {
 
 // Per-context device tables every NTT kernel reads.
 struct NttTables {
-    const ModC* mods;     // [n_mod] {q, mu}
-    const u64* psi;       // [n_mod][N]  psi^brv(i)
-    const u64* psi_sh;    // Shoup companions
-    const u64* ipsi;      // [n_mod][N]  psi^-brv(i)
-    const u64* ipsi_sh;
+    const ModC* mods;          // [n_mod] {q, mu}
+    const ulonglong2* psi;     // [n_mod][N] (psi^brv(i), Shoup companion)
+    const ulonglong2* ipsi;    // [n_mod][N] (psi^-brv(i), Shoup companion)
     u32 log_n;
 };
 

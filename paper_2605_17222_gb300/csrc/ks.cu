@@ -64,8 +64,13 @@ __global__ void __launch_bounds__(THREADS) k_ks_inner(const __grid_constant__ Ks
 // so Alg. 2 lines 8-14 (Phases 3 and 4 of Sec. IV) run without writing the
 // n1*n2 rotated ciphertexts to HBM.  DH-BSGS is the case n2 = 1, the diagonal
 // method n1 = 1, BSGS n2 = 1 over Q only.
+constexpr int MAXB = 8;  // digits handled unrolled; larger beta runs a plain loop
+
 template <int K3>
-__global__ void __launch_bounds__(THREADS) k_diag_mac(const __grid_constant__ DiagMacArgs a) {
+__global__ void __launch_bounds__(THREADS, 2) k_diag_mac(const __grid_constant__ DiagMacArgs a) {
+    // this giant index's switching-key words for the thread's own position,
+    // parked in thread-private shared-memory slots (no barrier needed)
+    __shared__ u64 skey[2 * MAXB * THREADS];
     const u32 N = 1u << a.log_n;
     const u32 s = blockIdx.x * THREADS + threadIdx.x;
     const u32 t = blockIdx.y;
@@ -77,19 +82,22 @@ __global__ void __launch_bounds__(THREADS) k_diag_mac(const __grid_constant__ Di
     const ModC m = a.mods[gmod];
     const size_t dstride = (size_t)(a.diag_level + a.k_p) * N;
     const size_t key_b = 2ull * (a.L + a.k_p) * N;
+    const size_t key_c = (size_t)(a.L + a.k_p) * N;
+    const size_t dig_b = (size_t)a.ext * N;
     const size_t tN = (size_t)t * N;
     const u32 n1n2 = a.n1 * a.n2;
     const bool lift_limb = a.lift0 && t < a.level;
     const u64 lc = lift_limb ? a.lift_c[gmod] : 0, lsh = lift_limb ? a.lift_sh[gmod] : 0;
+    const u32 beta = a.beta;
+    const bool small_beta = beta <= MAXB;
+    u64* sk = skey + threadIdx.x;
 
-    u32 h[K3];
-    const u64* fbase[K3];
+    const u64* fb[K3];
 #pragma unroll
     for (int kk = 0; kk < K3; kk++) {
         const u32 kc = k_first + min((u32)kk, k_count - 1);  // lanes past the chunk mirror its last index
         const u32 g = a.gal_diag[kc];
-        h[kk] = g ? auto_src(s, g, a.log_n) : s;
-        fbase[kk] = a.diags + (size_t)(n1n2 * kc) * dstride + (size_t)drow * N;
+        fb[kk] = a.diags + (size_t)(n1n2 * kc) * dstride + (size_t)drow * N + (g ? auto_src(s, g, a.log_n) : s);
     }
     U128 acc0[K3], acc1[K3];
 #pragma unroll
@@ -99,9 +107,23 @@ __global__ void __launch_bounds__(THREADS) k_diag_mac(const __grid_constant__ Di
     for (u32 j = 0; j < a.n2; j++) {
         const u32 src = j ? auto_src(s, a.gal_mid[j], a.log_n) : s;
         const u64* key = j ? a.keys[j] + (size_t)gmod * N + s : nullptr;
+        if (j && small_beta) {
+#pragma unroll
+            for (int b = 0; b < MAXB; b++) {
+                if (b < (int)beta) {
+                    sk[(2 * b) * THREADS] = key[b * key_b];
+                    sk[(2 * b + 1) * THREADS] = key[b * key_b + key_c];
+                }
+            }
+        }
         for (u32 i = 0; i < a.n1; i++) {
-            u64 av, bv;
             const bool lifted = (i == 0) && a.lift0;
+            // issue every independent load of this (i, j) before any arithmetic
+            const size_t didx = (size_t)(a.n1 * j + i) * dstride;
+            u64 f[K3];
+#pragma unroll
+            for (int kk = 0; kk < K3; kk++) f[kk] = kk < (int)k_count ? fb[kk][didx] : 0;
+            u64 av, bv;
             if (j == 0) {
                 if (lifted) {
                     av = lift_limb ? mul_shoup(a.A[0][tN + s], lc, lsh, m.q) : 0;
@@ -111,28 +133,36 @@ __global__ void __launch_bounds__(THREADS) k_diag_mac(const __grid_constant__ Di
                     bv = a.B[i][tN + s];
                 }
             } else {
-                U128 x0{0, 0}, x1{0, 0};
-                if (lifted) {
-                    if (lift_limb) add128(x0, mul_shoup(a.A[0][tN + src], lc, lsh, m.q));
-                } else {
-                    add128(x0, a.A[i][tN + src]);
-                }
                 const u64* D = a.Dg[i] + tN + src;
-                for (u32 b = 0; b < a.beta; b++) {
-                    const u64 d = D[(size_t)b * a.ext * N];
-                    mac128(x0, d, key[b * key_b]);
-                    mac128(x1, d, key[b * key_b + (size_t)(a.L + a.k_p) * N]);
+                const u64 xa = (!lifted || lift_limb) ? a.A[i][tN + src] : 0;
+                U128 x0{0, 0}, x1{0, 0};
+                if (small_beta) {
+                    u64 d[MAXB];
+#pragma unroll
+                    for (int b = 0; b < MAXB; b++) d[b] = b < (int)beta ? D[b * dig_b] : 0;
+#pragma unroll
+                    for (int b = 0; b < MAXB; b++) {
+                        if (b < (int)beta) {
+                            mac128(x0, d[b], sk[(2 * b) * THREADS]);
+                            mac128(x1, d[b], sk[(2 * b + 1) * THREADS]);
+                        }
+                    }
+                } else {
+                    for (u32 b = 0; b < beta; b++) {
+                        const u64 dv = D[b * dig_b];
+                        mac128(x0, dv, key[b * key_b]);
+                        mac128(x1, dv, key[b * key_b + key_c]);
+                    }
                 }
+                add128(x0, lifted ? mul_shoup(xa, lc, lsh, m.q) : xa);
                 av = reduce128(x0, m);
                 bv = reduce128(x1, m);
             }
-            const size_t didx = (size_t)(a.n1 * j + i) * dstride;
 #pragma unroll
             for (int kk = 0; kk < K3; kk++) {
                 if (kk < (int)k_count) {
-                    const u64 f = fbase[kk][didx + h[kk]];
-                    mac128(acc0[kk], av, f);
-                    mac128(acc1[kk], bv, f);
+                    mac128(acc0[kk], av, f[kk]);
+                    mac128(acc1[kk], bv, f[kk]);
                 }
             }
             if (++terms == 128) {

@@ -122,185 +122,245 @@ namespace {
 
 constexpr int MAXJ = 96;
 constexpr int THREADS = 256;
-constexpr u32 TILE = 4096;  // words per CTA in the row pass
 
 template <typename J>
 struct Jobs {
     J j[MAXJ];
 };
 
-struct Geo {
-    u32 log_n, log_r, log_c, w, b;  // R = 2^log_r rows, C = 2^log_c columns, w cols/CTA, b rows/CTA
-};
-
-Geo geometry(u32 log_n) {
-    Geo g;
-    g.log_n = log_n;
-    g.log_r = (log_n + 1) / 2;
-    g.log_c = log_n - g.log_r;
-    g.w = std::min<u32>(16u, 1u << g.log_c);
-    g.b = std::max<u32>(1u, std::min<u32>(1u << g.log_r, TILE >> g.log_c));
-    return g;
+// Twiddle w and its Shoup companion, one 16-byte load.
+__device__ __forceinline__ void tw_at(const ulonglong2* tab, u32 idx, u64& w, u64& ws) {
+    const ulonglong2 v = __ldg(tab + idx);
+    w = v.x;
+    ws = v.y;
 }
 
+// Cooley-Tukey butterfly (forward): (a, b) -> (a + w b, a - w b).
+__device__ __forceinline__ void ct_bfly(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
+    u64 w, ws;
+    tw_at(tab, idx, w, ws);
+    const u64 v = mul_shoup(b, w, ws, q);
+    b = sub_mod(a, v, q);
+    a = add_mod(a, v, q);
+}
+
+// Gentleman-Sande butterfly (inverse): (a, b) -> (a + b, (a - b) w).
+__device__ __forceinline__ void gs_bfly(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
+    u64 w, ws;
+    tw_at(tab, idx, w, ws);
+    const u64 s = add_mod(a, b, q);
+    b = mul_shoup(sub_mod(a, b, q), w, ws, q);
+    a = s;
+}
+
+// Every pass works on "lines" of S = 2^LOGS words (a column of the R x C
+// view in the column pass, a row in the row pass) with 16 words per thread
+// and TPL = S/16 threads per line, in two layouts:
+//   strided    : thread u holds line words u + TPL*v   (v = 0..15)
+//   contiguous : thread u holds line words 16*u + v
+// The four stages whose half-width is >= TPL pair words inside the strided
+// layout (v and v + half/TPL); the other LOGS - 4 stages pair words inside
+// the contiguous layout.  One shared-memory exchange sits between the two
+// rounds.  Row passes keep each line inside one warp, so their exchanges
+// need only __syncwarp; rows are padded by one word per 16 against bank
+// conflicts.
+__device__ __forceinline__ u32 pad16(u32 i) { return i + (i >> 4); }
+
 // ------------------------------------------------------------------ forward, column pass
-template <bool BCONV>
+// Global stages 0..LOGS-1 (m = 2^ss, twiddle psi^brv(m + r / 2t_r)).
+template <int LOGS, bool BCONV>
 __global__ void __launch_bounds__(THREADS) k_fwd_cols(const __grid_constant__ NttTables T,
-                                                      const __grid_constant__ Jobs<FwdJob> jobs, Geo g) {
-    extern __shared__ u64 sm[];
+                                                      const __grid_constant__ Jobs<FwdJob> jobs) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
+    __shared__ u64 sm[S * W];
+    const u32 log_n = T.log_n, N = 1u << log_n, C = N >> LOGS;
+    const u32 c = threadIdx.x % W, u = threadIdx.x / W;
+    const u32 col = blockIdx.x * W + c;
     const FwdJob& J = jobs.j[blockIdx.y];
-    const u32 N = 1u << g.log_n, R = 1u << g.log_r, C = 1u << g.log_c, W = g.w;
-    const u32 c0 = blockIdx.x * W;
     const ModC m = T.mods[J.mod];
-    const u64* psi = T.psi + (size_t)J.mod * N;
-    const u64* psh = T.psi_sh + (size_t)J.mod * N;
-    for (u32 e = threadIdx.x; e < R * W; e += THREADS) {
-        const u32 r = e / W, c = e % W;
-        const size_t x = (size_t)r * C + c0 + c;
-        u64 v;
+    const u64 q = m.q;
+    const ulonglong2* tw = T.psi + (size_t)J.mod * N;
+    u64 x[16];
+#pragma unroll
+    for (int v = 0; v < 16; v++) {
+        const size_t gi = (size_t)(u + TPL * v) * C + col;
         if constexpr (BCONV) {
             U128 acc{0, 0};
-            for (u32 j = 0; j < J.nsrc; j++) mac128(acc, J.src[(size_t)j * N + x], J.bcst[j]);
-            v = reduce128(acc, m);
+            for (u32 j = 0; j < J.nsrc; j++) mac128(acc, J.src[(size_t)j * N + gi], J.bcst[j]);
+            x[v] = reduce128(acc, m);
         } else {
-            v = J.src[x];
+            x[v] = J.src[gi];
         }
-        sm[e] = v;
     }
+#pragma unroll
+    for (int ss = 0; ss < 4; ss++) {
+        const int tv = 8 >> ss;
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & tv)) ct_bfly(x[v], x[v + tv], tw, (1u << ss) + (v >> (4 - ss)), q);
+    }
+#pragma unroll
+    for (int v = 0; v < 16; v++) sm[(u + TPL * v) * W + c] = x[v];
     __syncthreads();
-    for (u32 s = 0; s < g.log_r; s++) {
-        const u32 tr = R >> (s + 1);
-        const u32 mm = 1u << s;
-        for (u32 b = threadIdx.x; b < (R / 2) * W; b += THREADS) {
-            const u32 c = b % W, k = b / W;
-            const u32 grp = k / tr, pos = k % tr;
-            const u32 r = grp * 2 * tr + pos;
-            const u64 S = psi[mm + grp], Ssh = psh[mm + grp];
-            const u64 U = sm[r * W + c];
-            const u64 V = mul_shoup(sm[(r + tr) * W + c], S, Ssh, m.q);
-            sm[r * W + c] = add_mod(U, V, m.q);
-            sm[(r + tr) * W + c] = sub_mod(U, V, m.q);
-        }
-        __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = sm[(16 * u + v) * W + c];
+#pragma unroll
+    for (int ss = 4; ss < LOGS; ss++) {
+        const int t = S >> (ss + 1);
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & t)) ct_bfly(x[v], x[v + t], tw, (1u << ss) + ((16 * u + v) >> (LOGS - ss)), q);
     }
-    for (u32 e = threadIdx.x; e < R * W; e += THREADS) {
-        const u32 r = e / W, c = e % W;
-        J.dst[(size_t)r * C + c0 + c] = sm[e];
-    }
+#pragma unroll
+    for (int v = 0; v < 16; v++) J.dst[(size_t)(16 * u + v) * C + col] = x[v];
 }
 
 // ------------------------------------------------------------------ forward, row pass
-template <bool SUBMUL>
+// Global stages log_r..log_n-1 (m = 2^(log_r+ss), twiddle psi^brv(m + row 2^ss + x / 2t)).
+template <int LOGS, bool SUBMUL>
 __global__ void __launch_bounds__(THREADS) k_fwd_rows(const __grid_constant__ NttTables T,
-                                                      const __grid_constant__ Jobs<FwdJob> jobs, Geo g) {
-    extern __shared__ u64 sm[];
+                                                      const __grid_constant__ Jobs<FwdJob> jobs) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
+    __shared__ u64 sm[B * SP];
+    const u32 log_n = T.log_n, N = 1u << log_n, log_r = log_n - LOGS;
+    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
+    const u32 row = blockIdx.x * B + rl;
     const FwdJob& J = jobs.j[blockIdx.y];
-    const u32 N = 1u << g.log_n, C = 1u << g.log_c, B = g.b;
-    const u32 r0 = blockIdx.x * B;
-    const size_t base = (size_t)r0 * C;
-    const ModC m = T.mods[J.mod];
-    const u64* psi = T.psi + (size_t)J.mod * N;
-    const u64* psh = T.psi_sh + (size_t)J.mod * N;
-    for (u32 e = threadIdx.x; e < B * C; e += THREADS) sm[e] = J.dst[base + e];
-    __syncthreads();
-    const u32 half = C / 2;
-    for (u32 sp = 0; sp < g.log_c; sp++) {
-        const u32 mm = 1u << (g.log_r + sp);
-        const u32 t = C >> (sp + 1);
-        const u32 gpr = C / (2 * t);  // groups per row
-        for (u32 b = threadIdx.x; b < B * half; b += THREADS) {
-            const u32 blk = b / half, k = b % half;
-            const u32 grp = k / t, pos = k % t;
-            const u32 x = blk * C + grp * 2 * t + pos;
-            const u32 idx = mm + (r0 + blk) * gpr + grp;
-            const u64 U = sm[x];
-            const u64 V = mul_shoup(sm[x + t], psi[idx], psh[idx], m.q);
-            sm[x] = add_mod(U, V, m.q);
-            sm[x + t] = sub_mod(U, V, m.q);
-        }
-        __syncthreads();
+    const u64 q = T.mods[J.mod].q;
+    const ulonglong2* tw = T.psi + (size_t)J.mod * N;
+    const size_t base = (size_t)row * S;
+    u64* sr = sm + rl * SP;
+    u64 x[16];
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = J.dst[base + u + TPL * v];
+#pragma unroll
+    for (int ss = 0; ss < 4; ss++) {
+        const int tv = 8 >> ss;
+        const u32 b0 = (1u << (log_r + ss)) + (row << ss);
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & tv)) ct_bfly(x[v], x[v + tv], tw, b0 + (v >> (4 - ss)), q);
     }
-    for (u32 e = threadIdx.x; e < B * C; e += THREADS) {
-        const u64 v = sm[e];
+#pragma unroll
+    for (int v = 0; v < 16; v++) sr[pad16(u + TPL * v)] = x[v];
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = sr[pad16(16 * u + v)];
+#pragma unroll
+    for (int ss = 4; ss < LOGS; ss++) {
+        const int t = S >> (ss + 1);
+        const u32 b0 = (1u << (log_r + ss)) + (row << ss);
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & t)) ct_bfly(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (LOGS - ss)), q);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < 16; v++) sr[pad16(16 * u + v)] = x[v];
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < 16; v++) {
+        const u32 xi = u + TPL * v;
+        const u64 val = sr[pad16(xi)];
         if constexpr (SUBMUL) {
-            J.subout[base + e] = mul_shoup(sub_mod(J.subx[base + e], v, m.q), J.c, J.c_sh, m.q);
+            J.subout[base + xi] = mul_shoup(sub_mod(J.subx[base + xi], val, q), J.c, J.c_sh, q);
         } else {
-            J.dst[base + e] = v;
+            J.dst[base + xi] = val;
         }
     }
 }
 
 // ------------------------------------------------------------------ inverse, row pass
-template <bool GATHER>
+// GS stages with half-width t = 1..S/2 (m = N/2t, twiddle psi^-brv(m + row S/2t + x/2t)).
+template <int LOGS, bool GATHER>
 __global__ void __launch_bounds__(THREADS) k_inv_rows(const __grid_constant__ NttTables T,
-                                                      const __grid_constant__ Jobs<InvJob> jobs, Geo g) {
-    extern __shared__ u64 sm[];
+                                                      const __grid_constant__ Jobs<InvJob> jobs) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
+    __shared__ u64 sm[B * SP];
+    const u32 log_n = T.log_n, N = 1u << log_n;
+    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
+    const u32 row = blockIdx.x * B + rl;
     const InvJob& J = jobs.j[blockIdx.y];
-    const u32 N = 1u << g.log_n, C = 1u << g.log_c, B = g.b;
-    const u32 r0 = blockIdx.x * B;
-    const size_t base = (size_t)r0 * C;
-    const ModC m = T.mods[J.mod];
-    const u64* ipsi = T.ipsi + (size_t)J.mod * N;
-    const u64* ish = T.ipsi_sh + (size_t)J.mod * N;
-    for (u32 e = threadIdx.x; e < B * C; e += THREADS) {
-        if constexpr (GATHER) {
-            sm[e] = J.src[auto_src((u32)(base + e), J.gal, g.log_n)];
-        } else {
-            sm[e] = J.src[base + e];
-        }
+    const u64 q = T.mods[J.mod].q;
+    const ulonglong2* tw = T.ipsi + (size_t)J.mod * N;
+    const size_t base = (size_t)row * S;
+    u64* sr = sm + rl * SP;
+    u64 x[16];
+#pragma unroll
+    for (int v = 0; v < 16; v++) {
+        const u32 xi = u + TPL * v;
+        if constexpr (GATHER) x[v] = J.src[auto_src((u32)(base + xi), J.gal, log_n)];
+        else x[v] = J.src[base + xi];
     }
-    __syncthreads();
-    const u32 half = C / 2;
-    for (u32 u = 0; u < g.log_c; u++) {
-        const u32 t = 1u << u;
-        const u32 mm = N >> (u + 1);
-        const u32 gpr = C / (2 * t);
-        for (u32 b = threadIdx.x; b < B * half; b += THREADS) {
-            const u32 blk = b / half, k = b % half;
-            const u32 grp = k / t, pos = k % t;
-            const u32 x = blk * C + grp * 2 * t + pos;
-            const u32 idx = mm + (r0 + blk) * gpr + grp;
-            const u64 U = sm[x], V = sm[x + t];
-            sm[x] = add_mod(U, V, m.q);
-            sm[x + t] = mul_shoup(sub_mod(U, V, m.q), ipsi[idx], ish[idx], m.q);
-        }
-        __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 16; v++) sr[pad16(u + TPL * v)] = x[v];
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = sr[pad16(16 * u + v)];
+#pragma unroll
+    for (int lt = 0; lt < LOGS - 4; lt++) {  // t = 1 .. TPL/2
+        const int t = 1 << lt;
+        const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & t)) gs_bfly(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (lt + 1)), q);
     }
-    for (u32 e = threadIdx.x; e < B * C; e += THREADS) J.tmp[base + e] = sm[e];
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < 16; v++) sr[pad16(16 * u + v)] = x[v];
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = sr[pad16(u + TPL * v)];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {  // t = TPL * 2^k
+        const int lt = (LOGS - 4) + k;
+        const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & (1 << k))) gs_bfly(x[v], x[v + (1 << k)], tw, b0 + (v >> (k + 1)), q);
+    }
+#pragma unroll
+    for (int v = 0; v < 16; v++) J.tmp[base + u + TPL * v] = x[v];
 }
 
 // ------------------------------------------------------------------ inverse, column pass
+// GS stages with half-width C*t_r, t_r = 1..S/2 (m = S/2t_r, twiddle psi^-brv(m + r/2t_r)),
+// then the scaling by c (N^-1 and any per-limb constant).
+template <int LOGS>
 __global__ void __launch_bounds__(THREADS) k_inv_cols(const __grid_constant__ NttTables T,
-                                                      const __grid_constant__ Jobs<InvJob> jobs, Geo g) {
-    extern __shared__ u64 sm[];
+                                                      const __grid_constant__ Jobs<InvJob> jobs) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
+    __shared__ u64 sm[S * W];
+    const u32 log_n = T.log_n, N = 1u << log_n, C = N >> LOGS;
+    const u32 c = threadIdx.x % W, u = threadIdx.x / W;
+    const u32 col = blockIdx.x * W + c;
     const InvJob& J = jobs.j[blockIdx.y];
-    const u32 N = 1u << g.log_n, R = 1u << g.log_r, C = 1u << g.log_c, W = g.w;
-    const u32 c0 = blockIdx.x * W;
-    const ModC m = T.mods[J.mod];
-    const u64* ipsi = T.ipsi + (size_t)J.mod * N;
-    const u64* ish = T.ipsi_sh + (size_t)J.mod * N;
-    for (u32 e = threadIdx.x; e < R * W; e += THREADS) {
-        const u32 r = e / W, c = e % W;
-        sm[e] = J.tmp[(size_t)r * C + c0 + c];
+    const u64 q = T.mods[J.mod].q;
+    const ulonglong2* tw = T.ipsi + (size_t)J.mod * N;
+    u64 x[16];
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = J.tmp[(size_t)(16 * u + v) * C + col];
+#pragma unroll
+    for (int lt = 0; lt < LOGS - 4; lt++) {
+        const int t = 1 << lt;
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & t)) gs_bfly(x[v], x[v + t], tw, (S >> (lt + 1)) + ((16 * u + v) >> (lt + 1)), q);
     }
+#pragma unroll
+    for (int v = 0; v < 16; v++) sm[(16 * u + v) * W + c] = x[v];
     __syncthreads();
-    for (u32 u = g.log_c; u < g.log_n; u++) {
-        const u32 tr = 1u << (u - g.log_c);
-        const u32 mm = N >> (u + 1);
-        for (u32 b = threadIdx.x; b < (R / 2) * W; b += THREADS) {
-            const u32 c = b % W, k = b / W;
-            const u32 grp = k / tr, pos = k % tr;
-            const u32 r = grp * 2 * tr + pos;
-            const u64 U = sm[r * W + c], V = sm[(r + tr) * W + c];
-            sm[r * W + c] = add_mod(U, V, m.q);
-            sm[(r + tr) * W + c] = mul_shoup(sub_mod(U, V, m.q), ipsi[mm + grp], ish[mm + grp], m.q);
-        }
-        __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = sm[(u + TPL * v) * W + c];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int lt = (LOGS - 4) + k;
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & (1 << k))) gs_bfly(x[v], x[v + (1 << k)], tw, (S >> (lt + 1)) + (v >> (k + 1)), q);
     }
-    for (u32 e = threadIdx.x; e < R * W; e += THREADS) {
-        const u32 r = e / W, c = e % W;
-        J.dst[(size_t)r * C + c0 + c] = mul_shoup(sm[e], J.c, J.c_sh, m.q);
-    }
+#pragma unroll
+    for (int v = 0; v < 16; v++) J.dst[(size_t)(u + TPL * v) * C + col] = mul_shoup(x[v], J.c, J.c_sh, q);
 }
 
 __global__ void k_automorphism(const u64* __restrict__ in, u64* __restrict__ out, u32 gal, u32 log_n) {
@@ -323,21 +383,6 @@ __global__ void k_add_gather(const ModC* __restrict__ mods, const __grid_constan
     J.out[s] = v;
 }
 
-// Shared memory above 48 KB (log N = 17) needs an explicit opt-in per kernel.
-void set_smem_limits() {
-    static bool done = false;
-    if (done) return;
-    done = true;
-    const int lim = 96 * 1024;
-    cudaFuncSetAttribute(k_fwd_cols<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_fwd_cols<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_fwd_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_fwd_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_inv_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_inv_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    cudaFuncSetAttribute(k_inv_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-}
-
 template <typename J, typename F>
 void for_chunks(const J* jobs, int njobs, F&& f) {
     for (int s = 0; s < njobs; s += MAXJ) {
@@ -348,49 +393,63 @@ void for_chunks(const J* jobs, int njobs, F&& f) {
     }
 }
 
+template <int LR, int LC>
+void fwd_impl(const NttTables& T, const Jobs<FwdJob>& p, int n, bool bconv, bool submul, cudaStream_t st) {
+    const u32 N = 1u << T.log_n;
+    const dim3 g1((N >> LR) / (THREADS / ((1u << LR) / 16)), n), g2((N >> LC) / (THREADS / ((1u << LC) / 16)), n);
+    {
+        ProfScope ps(K_FWD_COLS, st);
+        if (bconv) k_fwd_cols<LR, true><<<g1, THREADS, 0, st>>>(T, p);
+        else k_fwd_cols<LR, false><<<g1, THREADS, 0, st>>>(T, p);
+    }
+    {
+        ProfScope ps(K_FWD_ROWS, st);
+        if (submul) k_fwd_rows<LC, true><<<g2, THREADS, 0, st>>>(T, p);
+        else k_fwd_rows<LC, false><<<g2, THREADS, 0, st>>>(T, p);
+    }
+}
+
+template <int LR, int LC>
+void inv_impl(const NttTables& T, const Jobs<InvJob>& p, int n, bool gather, cudaStream_t st) {
+    const u32 N = 1u << T.log_n;
+    const dim3 g1((N >> LR) / (THREADS / ((1u << LR) / 16)), n), g2((N >> LC) / (THREADS / ((1u << LC) / 16)), n);
+    {
+        ProfScope ps(K_INV_ROWS, st);
+        if (gather) k_inv_rows<LC, true><<<g2, THREADS, 0, st>>>(T, p);
+        else k_inv_rows<LC, false><<<g2, THREADS, 0, st>>>(T, p);
+    }
+    {
+        ProfScope ps(K_INV_COLS, st);
+        k_inv_cols<LR><<<g1, THREADS, 0, st>>>(T, p);
+    }
+}
+
+// N = 2^log_n is viewed as R x C with log R = ceil(log_n / 2).
+#define NTT_DISPATCH(IMPL, ...)                                   \
+    switch (T.log_n) {                                            \
+        case 12: IMPL<6, 6>(T, p, n, __VA_ARGS__, st); break;    \
+        case 13: IMPL<7, 6>(T, p, n, __VA_ARGS__, st); break;    \
+        case 14: IMPL<7, 7>(T, p, n, __VA_ARGS__, st); break;    \
+        case 15: IMPL<8, 7>(T, p, n, __VA_ARGS__, st); break;    \
+        default: IMPL<8, 8>(T, p, n, __VA_ARGS__, st); break;    \
+    }
+
 }  // namespace
 
 void launch_fwd_ntt(const NttTables& T, const FwdJob* jobs, int njobs, cudaStream_t st) {
     if (njobs <= 0) return;
-    const Geo g = geometry(T.log_n);
-    const u32 R = 1u << g.log_r, C = 1u << g.log_c;
-    const size_t sm1 = (size_t)R * g.w * sizeof(u64), sm2 = (size_t)g.b * C * sizeof(u64);
     const bool bconv = jobs[0].nsrc > 0, submul = jobs[0].subout != nullptr;
-    set_smem_limits();
     for_chunks(jobs, njobs, [&](const Jobs<FwdJob>& p, int n) {
-        dim3 g1(C / g.w, n), g2(R / g.b, n);
-        {
-            ProfScope ps(K_FWD_COLS, st);
-            if (bconv) k_fwd_cols<true><<<g1, THREADS, sm1, st>>>(T, p, g);
-            else k_fwd_cols<false><<<g1, THREADS, sm1, st>>>(T, p, g);
-        }
-        {
-            ProfScope ps(K_FWD_ROWS, st);
-            if (submul) k_fwd_rows<true><<<g2, THREADS, sm2, st>>>(T, p, g);
-            else k_fwd_rows<false><<<g2, THREADS, sm2, st>>>(T, p, g);
-        }
+        NTT_DISPATCH(fwd_impl, bconv, submul);
         count_launch(2);
     });
 }
 
 void launch_inv_ntt(const NttTables& T, const InvJob* jobs, int njobs, cudaStream_t st) {
     if (njobs <= 0) return;
-    const Geo g = geometry(T.log_n);
-    const u32 R = 1u << g.log_r, C = 1u << g.log_c;
-    const size_t sm1 = (size_t)R * g.w * sizeof(u64), sm2 = (size_t)g.b * C * sizeof(u64);
     const bool gather = jobs[0].gal != 0;
-    set_smem_limits();
     for_chunks(jobs, njobs, [&](const Jobs<InvJob>& p, int n) {
-        dim3 g1(C / g.w, n), g2(R / g.b, n);
-        {
-            ProfScope ps(K_INV_ROWS, st);
-            if (gather) k_inv_rows<true><<<g2, THREADS, sm2, st>>>(T, p, g);
-            else k_inv_rows<false><<<g2, THREADS, sm2, st>>>(T, p, g);
-        }
-        {
-            ProfScope ps(K_INV_COLS, st);
-            k_inv_cols<<<g1, THREADS, sm1, st>>>(T, p, g);
-        }
+        NTT_DISPATCH(inv_impl, gather);
         count_launch(2);
     });
 }
