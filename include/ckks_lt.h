@@ -211,6 +211,21 @@ ckks_status ckks_automorphism(ckks_ctx* ctx, uint32_t n_limbs, const uint64_t* i
                               uint64_t* out, void* stream);
 
 /* ------------------------------------------------------------------ misc */
+
+/* Waits for the context's device and reports whether any device-side wait
+ * gave up since the last check (CKKS_ETIMEOUT; the flag is then cleared and
+ * the results computed since the last check must be discarded).  Kernels
+ * that stage operands through asynchronous copies bound every wait on them
+ * (about one second) instead of spinning forever.  ckks_ct_download performs
+ * the same check. */
+ckks_status ckks_device_status(ckks_ctx* ctx);
+
+/* Failure-detection self-test: queues one kernel that waits, with the same
+ * bounded wait, on a device barrier that nothing completes, for limit_ms
+ * (1..5000) milliseconds.  The next ckks_device_status then reports
+ * CKKS_ETIMEOUT and the context stays usable.  Faults nothing. */
+ckks_status ckks_selftest_bounded_wait(ckks_ctx* ctx, uint32_t limit_ms, void* stream);
+
 const char* ckks_last_error(void);
 size_t ckks_device_bytes_in_use(const ckks_ctx* ctx);
 /* Number of CUDA kernels this library has launched in this process. */

@@ -79,6 +79,8 @@ def lib():
         "ckks_moddown_rescale": [P, U32, P, P, P],
         "ckks_rescale": [P, U32, P, P, P],
         "ckks_automorphism": [P, U32, P, I32, P, P],
+        "ckks_device_status": [P],
+        "ckks_selftest_bounded_wait": [P, U32, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -208,6 +210,13 @@ class Context:
 
     def beta(self, level: int) -> int:
         return -(-level // self.alpha)
+
+    def device_status(self) -> None:
+        """Raise CkksError(CKKS_ETIMEOUT) if a bounded device-side wait gave up."""
+        check(lib().ckks_device_status(self.h))
+
+    def selftest_bounded_wait(self, limit_ms: int = 200, stream=None) -> None:
+        check(lib().ckks_selftest_bounded_wait(self.h, limit_ms, _stream(stream)))
 
     def bytes_in_use(self) -> int:
         return lib().ckks_device_bytes_in_use(self.h)

@@ -132,7 +132,7 @@ struct ckks_ctx {
     int device = 0;
     u32 log_n = 0, N = 0, L = 0, K = 0, dnum = 0, alpha = 0, beta_max = 0;
     std::vector<u64> mods;  // q_0..q_{L-1}, p_0..p_{K-1}
-    DevBuf d_mods, d_psi, d_ipsi, d_lift, d_lift_sh;
+    DevBuf d_mods, d_psi, d_ipsi, d_lift, d_lift_sh, d_err;
     NttTables T{};
     std::map<u32, LevelConsts> levels;
     std::map<u32, u64*> keys;  // rotation (mod N/2) -> [beta_max][2][L+K][N]
@@ -408,6 +408,7 @@ DiagMacArgs dm_base(ckks_ctx* C, u32 level, bool with_p, const ckks_diags* f) {
     a.beta = C->beta(level);
     a.log_n = C->log_n;
     a.diag_level = f->level;
+    a.err = (u32*)C->d_err.p;
     return a;
 }
 
@@ -637,6 +638,36 @@ extern "C" {
 
 const char* ckks_last_error(void) { return g_err.c_str(); }
 
+// Reads (and clears) the context's device error word: nonzero means a bounded
+// device-side wait gave up, so results computed since the last check are void.
+static void check_device_flag(ckks_ctx* ctx) {
+    uint32_t flag = 0;
+    CK(cudaMemcpy(&flag, ctx->d_err.p, 4, cudaMemcpyDeviceToHost));
+    if (flag) {
+        CK(cudaMemset(ctx->d_err.p, 0, 4));
+        fail(CKKS_ETIMEOUT, "a bounded device-side wait gave up; results since the last check are void");
+    }
+}
+
+ckks_status ckks_device_status(ckks_ctx* ctx) {
+    return guarded([&] {
+        if (!ctx) fail(CKKS_EINVAL, "null argument");
+        CK(cudaSetDevice(ctx->device));
+        CK(cudaDeviceSynchronize());
+        check_device_flag(ctx);
+    });
+}
+
+ckks_status ckks_selftest_bounded_wait(ckks_ctx* ctx, uint32_t limit_ms, void* stream) {
+    return guarded([&] {
+        if (!ctx) fail(CKKS_EINVAL, "null argument");
+        if (limit_ms < 1 || limit_ms > 5000) fail(CKKS_EINVAL, "limit must be 1..5000 ms");
+        CK(cudaSetDevice(ctx->device));
+        launch_wait_selftest((u32*)ctx->d_err.p, (u64)limit_ms * 1000000ull, (cudaStream_t)stream);
+        CK(cudaGetLastError());
+    });
+}
+
 ckks_status ckks_profile_enable(const char* kernel_class, int on) {
     return guarded([&] {
         const int c = prof_class(kernel_class);
@@ -724,6 +755,8 @@ ckks_status ckks_ctx_create(ckks_ctx** out, uint32_t log_n, const uint64_t* q, u
         CK(cudaMemcpy(C->d_mods.p, mc.data(), nm * sizeof(ModC), cudaMemcpyHostToDevice));
         C->d_psi.p = C->upload(psi);
         C->d_ipsi.p = C->upload(ipsi);
+        C->d_err.p = C->dalloc(1);
+        CK(cudaMemset(C->d_err.p, 0, 8));
         C->d_lift.p = C->upload(lift);
         C->d_lift_sh.p = C->upload(lsh);
         C->T = NttTables{(const ModC*)C->d_mods.p, (const ulonglong2*)C->d_psi.p, (const ulonglong2*)C->d_ipsi.p,
@@ -744,7 +777,7 @@ ckks_status ckks_ctx_destroy(ckks_ctx* ctx) {
             cudaFree(kv.second.mdr_tab);
             cudaFree(kv.second.rs_tab);
         }
-        for (DevBuf* b : {&ctx->d_mods, &ctx->d_psi, &ctx->d_ipsi, &ctx->d_lift, &ctx->d_lift_sh})
+        for (DevBuf* b : {&ctx->d_mods, &ctx->d_psi, &ctx->d_ipsi, &ctx->d_lift, &ctx->d_lift_sh, &ctx->d_err})
             cudaFree(b->p);
         delete ctx;
     });
@@ -873,6 +906,7 @@ ckks_status ckks_ct_download(const ckks_ct* ct, uint64_t* host, size_t n_words) 
         if (n_words != 2ull * ct->level * ct->ctx->N) fail(CKKS_EINVAL, "size mismatch");
         CK(cudaSetDevice(ct->ctx->device));
         CK(cudaDeviceSynchronize());
+        check_device_flag(ct->ctx);
         CK(cudaMemcpy(host, ct->d, n_words * 8, cudaMemcpyDeviceToHost));
     });
 }

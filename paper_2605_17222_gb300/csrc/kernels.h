@@ -97,8 +97,10 @@ struct DiagMacArgs {
     u32 gal_diag[DM_MAX_N3];         // rotation -(n1*n2*k*stride), 0 = none
     u32 level, ext, L, k_p, beta, log_n;
     u32 n1, n2, n3, lift0, diag_level;
+    u32* err;                        // set to nonzero when a bounded device wait gives up
 };
 void launch_diag_mac(const DiagMacArgs& a, cudaStream_t st);
+void launch_wait_selftest(u32* err, u64 limit_ns, cudaStream_t st);
 
 uint64_t launches();
 void count_launch(int n = 1);

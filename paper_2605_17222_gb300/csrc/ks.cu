@@ -184,7 +184,281 @@ __global__ void __launch_bounds__(THREADS, 2) k_diag_mac(const __grid_constant__
     }
 }
 
+// ------------------------------------------------------------------ K6, staged through shared memory by TMA
+// Same computation as k_diag_mac, organised around Eq. (8): in bit-reversed
+// storage every automorphism maps an aligned run of RUN words onto one
+// aligned run of RUN words.  A CTA owns one run of RUN positions of limb t, so
+// every operand of one (i, j) step is a handful of contiguous RUN-word source
+// runs: K3 diagonal runs, beta digit runs and the A run (B too at j = 0), plus
+// 2*beta key runs per giant index j.  One thread copies them into shared
+// memory with bulk (TMA) copies, cp.async.bulk, completing on an mbarrier, one
+// step ahead of the computation (ring of DM_NS stage buffers; keys
+// double-buffered by the parity of j).  The CTA then computes the step from
+// shared memory, applying the in-run permutation.
+//
+// Every wait is bounded.  A wait that gives up sets *a.err and the whole CTA
+// leaves the loop together (the decision goes through __syncthreads_or); the
+// producer then waits, bounded again, for the copies it has in flight before
+// the CTA exits.
+constexpr int DM_NS = 2;                              // stage ring depth
+constexpr u64 DM_WAIT_NS = 1000000000ull;              // a wait gives up after 1 s
+
+__device__ __forceinline__ u64 global_ns() {
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ u32 smem_u32(const void* p) { return (u32)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(u64* bar, u32 bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity) {
+    u32 ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(u64* bar, u32 parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const u64 t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > DM_WAIT_NS) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, u32 bytes, u64* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int K3, int RUN>
+__global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constant__ DiagMacArgs a) {
+    extern __shared__ __align__(128) u64 smem[];
+    __shared__ __align__(8) u64 full_bar[DM_NS];
+    const u32 N = 1u << a.log_n;
+    const u32 l = threadIdx.x;
+    const u32 run = blockIdx.x;
+    const u32 s = run * RUN + l;
+    const u32 t = blockIdx.y;
+    const u32 k_first = blockIdx.z * K3;
+    const u32 k_count = min((u32)K3, a.n3 - k_first);
+    const u32 gmod = t < a.level ? t : a.L + (t - a.level);
+    const u32 drow = t < a.level ? t : a.diag_level + (t - a.level);
+    const ModC m = a.mods[gmod];
+    const size_t dstride = (size_t)(a.diag_level + a.k_p) * N;
+    const size_t key_b = 2ull * (a.L + a.k_p) * N;
+    const size_t key_c = (size_t)(a.L + a.k_p) * N;
+    const size_t dig_b = (size_t)a.ext * N;
+    const size_t tN = (size_t)t * N;
+    const u32 n1 = a.n1, n2 = a.n2, n1n2 = n1 * n2;
+    const u32 beta = n2 > 1 ? a.beta : 0;
+    const bool lift_limb = a.lift0 && t < a.level;
+    const u64 lc = lift_limb ? a.lift_c[gmod] : 0, lsh = lift_limb ? a.lift_sh[gmod] : 0;
+    constexpr u32 RB = RUN * 8;  // bytes per run
+
+    // shared-memory layout: DM_NS stages of [K3 diag | beta digit | A | B] runs, then 2 key buffers of 2*beta runs
+    const u32 stage_runs = K3 + beta + 2;
+    u64* stage0 = smem;
+    u64* keybuf = smem + (size_t)DM_NS * stage_runs * RUN;
+
+    // per-thread in-run positions of the diagonal gathers (constant over the loop)
+    u32 pd[K3];
+    u32 hrun[K3];
+#pragma unroll
+    for (int kk = 0; kk < K3; kk++) {
+        const u32 kc = k_first + min((u32)kk, k_count - 1);
+        const u32 g = a.gal_diag[kc];
+        const u32 base = g ? auto_src(run * RUN, g, a.log_n) : run * RUN;
+        hrun[kk] = base / RUN;
+        pd[kk] = (g ? auto_src(s, g, a.log_n) : s) - hrun[kk] * RUN;
+    }
+
+    // Producer (thread 0): copies of step `it` = j * n1 + i into stage it % DM_NS.
+    // Runs, in order: k_count diagonal runs; at j = 0 the A and B runs; at j > 0
+    // the beta digit runs, the A run, and at i = 0 the 2*beta key runs of j.
+    // A and B are skipped for the lifted ciphertext on P limbs (zero words).
+    auto issue = [&](u32 it) {
+        if (it >= n1n2) return;
+        const u32 j = it / n1, i = it % n1;
+        u64* st = stage0 + (size_t)(it % DM_NS) * stage_runs * RUN;
+        u64* bar = &full_bar[it % DM_NS];
+        const bool lifted = (i == 0) && a.lift0;
+        const bool copy_a = !lifted || lift_limb;
+        const u32 srun = j ? auto_src(run * RUN, a.gal_mid[j], a.log_n) / RUN : run;
+        const u32 n_ab = j == 0 ? (copy_a ? 2u : 0u) : (copy_a ? 1u : 0u);
+        const u32 n_dig = j == 0 ? 0u : beta;
+        const u32 n_key = (j > 0 && i == 0) ? 2u * beta : 0u;
+        mbar_expect_tx(bar, (k_count + n_dig + n_ab + n_key) * RB);
+        const size_t didx = (size_t)(n1 * j + i) * dstride + (size_t)drow * N;
+#pragma unroll
+        for (int kk = 0; kk < K3; kk++)
+            if (kk < (int)k_count)
+                tma_load_1d(st + (size_t)kk * RUN,
+                            a.diags + (size_t)(n1n2 * (k_first + kk)) * dstride + didx + (size_t)hrun[kk] * RUN, RB,
+                            bar);
+        for (u32 b = 0; b < n_dig; b++)
+            tma_load_1d(st + (size_t)(K3 + b) * RUN, a.Dg[i] + b * dig_b + tN + (size_t)srun * RUN, RB, bar);
+        if (n_ab >= 1) tma_load_1d(st + (size_t)(K3 + beta) * RUN, a.A[i] + tN + (size_t)srun * RUN, RB, bar);
+        if (n_ab == 2) tma_load_1d(st + (size_t)(K3 + beta + 1) * RUN, a.B[i] + tN + (size_t)srun * RUN, RB, bar);
+        if (n_key) {
+            u64* kb = keybuf + (size_t)(j & 1) * 2 * beta * RUN;
+            const u64* ks = a.keys[j] + (size_t)gmod * N + (size_t)run * RUN;
+            for (u32 b = 0; b < beta; b++) {
+                tma_load_1d(kb + (size_t)(2 * b) * RUN, ks + b * key_b, RB, bar);
+                tma_load_1d(kb + (size_t)(2 * b + 1) * RUN, ks + b * key_b + key_c, RB, bar);
+            }
+        }
+    };
+
+    if (l == 0) {
+#pragma unroll
+        for (int b = 0; b < DM_NS; b++) mbar_init(&full_bar[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (l == 0)
+        for (int p = 0; p < DM_NS - 1; p++) issue(p);
+
+    U128 acc0[K3], acc1[K3];
+#pragma unroll
+    for (int kk = 0; kk < K3; kk++) acc0[kk] = acc1[kk] = U128{0, 0};
+    u32 terms = 0;
+    u32 issued = DM_NS - 1;  // steps the producer has issued (meaningful in thread 0)
+    bool failed = false;
+
+    for (u32 it = 0; it < n1n2; it++) {
+        const bool ok = mbar_wait_bounded(&full_bar[it % DM_NS], (it / DM_NS) & 1);
+        // everyone has finished step it-1 (its buffer is free) and agrees on success
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (l == 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            issue(it + DM_NS - 1);
+            issued = it + DM_NS;
+        }
+        const u32 j = it / n1, i = it % n1;
+        const u64* st = stage0 + (size_t)(it % DM_NS) * stage_runs * RUN;
+        const bool lifted = (i == 0) && a.lift0;
+        u64 av, bv;
+        if (j == 0) {
+            if (lifted) {
+                av = lift_limb ? mul_shoup(st[(K3 + beta) * RUN + l], lc, lsh, m.q) : 0;
+                bv = lift_limb ? mul_shoup(st[(K3 + beta + 1) * RUN + l], lc, lsh, m.q) : 0;
+            } else {
+                av = st[(K3 + beta) * RUN + l];
+                bv = st[(K3 + beta + 1) * RUN + l];
+            }
+        } else {
+            const u32 pm = auto_src(s, a.gal_mid[j], a.log_n) % RUN;
+            const u64* kb = keybuf + (size_t)(j & 1) * 2 * beta * RUN + l;
+            U128 x0{0, 0}, x1{0, 0};
+            for (u32 b = 0; b < beta; b++) {
+                const u64 d = st[(K3 + b) * RUN + pm];
+                mac128(x0, d, kb[(2 * b) * RUN]);
+                mac128(x1, d, kb[(2 * b + 1) * RUN]);
+            }
+            if (lifted) {
+                if (lift_limb) add128(x0, mul_shoup(st[(K3 + beta) * RUN + pm], lc, lsh, m.q));
+            } else {
+                add128(x0, st[(K3 + beta) * RUN + pm]);
+            }
+            av = reduce128(x0, m);
+            bv = reduce128(x1, m);
+        }
+#pragma unroll
+        for (int kk = 0; kk < K3; kk++) {
+            if (kk < (int)k_count) {
+                const u64 f = st[kk * RUN + pd[kk]];
+                mac128(acc0[kk], av, f);
+                mac128(acc1[kk], bv, f);
+            }
+        }
+        if (++terms == 128) {
+            terms = 0;
+#pragma unroll
+            for (int kk = 0; kk < K3; kk++) {
+                acc0[kk] = U128{reduce128(acc0[kk], m), 0};
+                acc1[kk] = U128{reduce128(acc1[kk], m), 0};
+            }
+        }
+    }
+    if (failed) {
+        // drain: the producer waits (bounded) for every step it issued that was not consumed
+        if (l == 0) {
+            for (u32 it = 0; it < min(issued, n1n2); it++)
+                mbar_wait_bounded(&full_bar[it % DM_NS], (it / DM_NS) & 1);
+            atomicExch(a.err, 1u);
+        }
+        return;
+    }
+#pragma unroll
+    for (int kk = 0; kk < K3; kk++) {
+        if (kk < (int)k_count) {
+            a.U0[k_first + kk][tN + s] = reduce128(acc0[kk], m);
+            a.U1[k_first + kk][tN + s] = reduce128(acc1[kk], m);
+        }
+    }
+}
+
+// Failure-detection self-test: one thread waits on an mbarrier that nothing
+// will complete, with the same bounded wait the staged kernels use (limit
+// given in ns), and records the give-up in *err.
+__global__ void k_wait_selftest(u32* err, u64 limit_ns) {
+    __shared__ __align__(8) u64 bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    const u64 t0 = global_ns();
+    bool ok = false;
+    while (!(ok = mbar_try_wait(&bar, 0)))
+        if (global_ns() - t0 > limit_ns) break;
+    if (!ok) atomicExch(err, 1u);
+}
+
+template <int K3, int RUN>
+size_t staged_smem(const DiagMacArgs& a) {
+    const size_t beta = a.n2 > 1 ? a.beta : 0;
+    return 8ull * RUN * (DM_NS * (K3 + beta + 2) + 2 * 2 * beta);
+}
+
+constexpr size_t DM_SMEM_MAX = 226 * 1024;  // dynamic part; the mbarriers take a few static bytes
+
+template <int K3, int RUN>
+bool try_staged(const DiagMacArgs& a, cudaStream_t st) {
+    const size_t sm = staged_smem<K3, RUN>(a);
+    const u32 N = 1u << a.log_n;
+    if (sm > DM_SMEM_MAX || N % RUN || (a.n2 > 1 && a.beta > 16)) return false;
+    static int attr_ok = -1;
+    if (attr_ok < 0)
+        attr_ok = cudaFuncSetAttribute(k_diag_mac_staged<K3, RUN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)DM_SMEM_MAX) == cudaSuccess;
+    if (!attr_ok) return false;
+    const dim3 grid(N / RUN, a.ext, (a.n3 + K3 - 1) / K3);
+    k_diag_mac_staged<K3, RUN><<<grid, RUN, sm, st>>>(a);
+    return true;
+}
+
 }  // namespace
+
+void launch_wait_selftest(u32* err, u64 limit_ns, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(err, limit_ns);
+    count_launch();
+}
 
 void launch_ks_inner(const KsArgs& a, cudaStream_t st) {
     const u32 N = 1u << a.log_n;
@@ -199,6 +473,17 @@ void launch_diag_mac(const DiagMacArgs& a, cudaStream_t st) {
     while (k3 < a.n3 && k3 < (u32)DM_MAX_K3) k3 *= 2;
     const dim3 grid((N + THREADS - 1) / THREADS, a.ext, (a.n3 + k3 - 1) / k3);
     ProfScope ps(K_DIAG_MAC, st);
+    bool done = false;
+    switch (k3) {
+        case 1: done = try_staged<1, 512>(a, st) || try_staged<1, 256>(a, st); break;
+        case 2: done = try_staged<2, 512>(a, st) || try_staged<2, 256>(a, st); break;
+        case 4: done = try_staged<4, 512>(a, st) || try_staged<4, 256>(a, st); break;
+        default: done = try_staged<8, 512>(a, st) || try_staged<8, 256>(a, st); break;
+    }
+    if (done) {
+        count_launch();
+        return;
+    }
     switch (k3) {
         case 1: k_diag_mac<1><<<grid, THREADS, 0, st>>>(a); break;
         case 2: k_diag_mac<2><<<grid, THREADS, 0, st>>>(a); break;

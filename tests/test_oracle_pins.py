@@ -128,7 +128,7 @@ def test_automorphism_coeff_definition(tiny):
         assert [int(x) for x in got[0]] == [w % q for w in want]
 
 
-@pytest.mark.parametrize("dp", [8, 32, 128, 256])
+@pytest.mark.parametrize("dp", [8, 32, 128, 256, 512])
 def test_automorphism_row_to_row_property(dp):
     """Eq. (8) and its proof: in bit-reversed storage with rows of d_p words,
     the gather of each row reads exactly one whole source row (a permutation
