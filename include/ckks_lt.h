@@ -202,6 +202,23 @@ ckks_status ckks_moddown(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint6
 ckks_status ckks_moddown_rescale(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out,
                                  void* stream);
 
+/* ModDown exactly as ckks_moddown, for callers that must not allocate device
+ * memory while they run (code recorded into a CUDA graph, code under an
+ * external memory budget or allocator, paths where cudaMalloc is off limits).
+ * The paper has no counterpart: this is a deployment variant.  Its scratch is
+ * a fixed device array inside the library of 8 limbs at N = 2^16 (4 MiB,
+ * k * N <= 524288 words); every GPU that loads the library holds it until
+ * the process exits.  Larger k * N, level > 64 or k > 8 fail with
+ * CKKS_EINVAL, and so does a level whose constant tables do not exist yet
+ * (any earlier call at that level on this context creates them).  The call
+ * allocates nothing: its first call on a device looks up the array's device
+ * address once (make that first call before any stream capture).  All calls
+ * share the one array, so calls whose work overlaps on the GPU (other
+ * streams, other contexts on the same device) race; serialise them.  The
+ * scratch is fully rewritten before it is read, so leftover contents from
+ * an earlier call do not matter. */
+ckks_status ckks_moddown_noalloc(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out, void* stream);
+
 /* Rescale, Eq. (1): x [level][N] -> out [level-1][N]. */
 ckks_status ckks_rescale(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out, void* stream);
 

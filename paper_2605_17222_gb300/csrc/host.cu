@@ -1065,6 +1065,77 @@ ckks_status ckks_moddown(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint6
     });
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------ ModDown without allocation
+// For callers that must not allocate device memory while they run: code
+// recorded into a CUDA graph, code running under an external memory budget
+// or allocator, or code on a path that may not call cudaMalloc at all.
+// ModDown's only scratch (the inverse-transformed special-prime limbs) lives
+// in this fixed file-scope array instead of the stream-ordered pool: at most
+// NOALLOC_SCRATCH_WORDS words (8 limbs of N = 2^16, 4 MiB), held by every
+// GPU that loads the library until the process exits.
+constexpr size_t NOALLOC_SCRATCH_WORDS = 8ull << 16;
+static __device__ __align__(256) uint64_t g_moddown_scratch[NOALLOC_SCRATCH_WORDS];
+
+namespace {
+std::mutex g_scratch_mu;
+u64* g_scratch_dev[128] = {};
+
+// Device address of g_moddown_scratch on `dev` (the current device).  The
+// array's name in host code is only a host-side stand-in, so the address is
+// looked up once per device and cached.
+u64* noalloc_scratch(int dev) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (dev < 0 || dev >= 128) fail(CKKS_EINVAL, "device index out of range");
+    if (!g_scratch_dev[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_moddown_scratch));
+        g_scratch_dev[dev] = (u64*)p;
+    }
+    return g_scratch_dev[dev];
+}
+}  // namespace
+
+extern "C" {
+
+ckks_status ckks_moddown_noalloc(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out, void* stream) {
+    return guarded([&] {
+        if (!ctx || !x || !out) fail(CKKS_EINVAL, "null argument");
+        if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        if (x == out) fail(CKKS_EINVAL, "ModDown cannot run in place");
+        if ((size_t)ctx->K * ctx->N > NOALLOC_SCRATCH_WORDS)
+            fail(CKKS_EINVAL, "k * N = " + std::to_string((size_t)ctx->K * ctx->N) +
+                                  " words exceeds the fixed scratch of " + std::to_string(NOALLOC_SCRATCH_WORDS) +
+                                  " words (8 limbs at N = 2^16)");
+        if (level > 64 || ctx->K > 8) fail(CKKS_EINVAL, "level must be <= 64 and k <= 8");
+        const LevelConsts* LC = nullptr;
+        {
+            std::lock_guard<std::mutex> g(ctx->mu);
+            auto it = ctx->levels.find(level);
+            if (it != ctx->levels.end()) LC = &it->second;
+        }
+        if (!LC)
+            fail(CKKS_EINVAL, "the constants of this level are not set up yet; any earlier call at this level "
+                              "(ckks_moddown, lt_eval, ...) sets them up");
+        CK(cudaSetDevice(ctx->device));
+        u64* Y = noalloc_scratch(ctx->device);
+        const u32 N = ctx->N, k = ctx->K;
+        cudaStream_t st = (cudaStream_t)stream;
+        InvJob ij[8];
+        for (u32 i = 0; i < k; i++)
+            ij[i] = InvJob{x + (size_t)(level + i) * N, Y + (size_t)i * N, Y + (size_t)i * N, LC->md_c[i], LC->md_sh[i],
+                           ctx->L + i, 0};
+        launch_inv_ntt(ctx->T, ij, (int)k, st);
+        FwdJob fj[64];
+        for (u32 j = 0; j < level; j++)
+            fj[j] = FwdJob{Y, out + (size_t)j * N, LC->md_tab + (size_t)j * k, x + (size_t)j * N, out + (size_t)j * N,
+                           LC->md_pinv[j], LC->md_pinv_sh[j], j, k};
+        launch_fwd_ntt(ctx->T, fj, (int)level, st);
+        CK(cudaGetLastError());
+    });
+}
+
 ckks_status ckks_moddown_rescale(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out, void* stream) {
     return guarded([&] {
         if (!ctx || !x || !out) fail(CKKS_EINVAL, "null argument");
