@@ -244,10 +244,10 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, u32 byte
         : "memory");
 }
 
-template <int K3, int RUN>
+template <int K3, int RUN, int NS, int KB>
 __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constant__ DiagMacArgs a) {
     extern __shared__ __align__(128) u64 smem[];
-    __shared__ __align__(8) u64 full_bar[DM_NS];
+    __shared__ __align__(8) u64 full_bar[NS];
     const u32 N = 1u << a.log_n;
     const u32 l = threadIdx.x;
     const u32 run = blockIdx.x;
@@ -264,15 +264,13 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
     const size_t dig_b = (size_t)a.ext * N;
     const size_t tN = (size_t)t * N;
     const u32 n1 = a.n1, n2 = a.n2, n1n2 = n1 * n2;
-    const u32 beta = n2 > 1 ? a.beta : 0;
+    const u32 beta = n2 > 1 ? a.beta : 0;  // <= KB (host checks)
     const bool lift_limb = a.lift0 && t < a.level;
     const u64 lc = lift_limb ? a.lift_c[gmod] : 0, lsh = lift_limb ? a.lift_sh[gmod] : 0;
     constexpr u32 RB = RUN * 8;  // bytes per run
 
-    // shared-memory layout: DM_NS stages of [K3 diag | beta digit | A | B] runs, then 2 key buffers of 2*beta runs
+    // shared memory: NS stages of [K3 diag | beta digit | A | B] runs
     const u32 stage_runs = K3 + beta + 2;
-    u64* stage0 = smem;
-    u64* keybuf = smem + (size_t)DM_NS * stage_runs * RUN;
 
     // per-thread in-run positions of the diagonal gathers (constant over the loop)
     u32 pd[K3];
@@ -286,22 +284,21 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
         pd[kk] = (g ? auto_src(s, g, a.log_n) : s) - hrun[kk] * RUN;
     }
 
-    // Producer (thread 0): copies of step `it` = j * n1 + i into stage it % DM_NS.
+    // Producer (thread 0): copies of step `it` = j * n1 + i into stage it % NS.
     // Runs, in order: k_count diagonal runs; at j = 0 the A and B runs; at j > 0
-    // the beta digit runs, the A run, and at i = 0 the 2*beta key runs of j.
-    // A and B are skipped for the lifted ciphertext on P limbs (zero words).
+    // the beta digit runs and the A run.  A and B are skipped for the lifted
+    // ciphertext on P limbs (zero words).
     auto issue = [&](u32 it) {
         if (it >= n1n2) return;
         const u32 j = it / n1, i = it % n1;
-        u64* st = stage0 + (size_t)(it % DM_NS) * stage_runs * RUN;
-        u64* bar = &full_bar[it % DM_NS];
+        u64* st = smem + (size_t)(it % NS) * stage_runs * RUN;
+        u64* bar = &full_bar[it % NS];
         const bool lifted = (i == 0) && a.lift0;
         const bool copy_a = !lifted || lift_limb;
         const u32 srun = j ? auto_src(run * RUN, a.gal_mid[j], a.log_n) / RUN : run;
         const u32 n_ab = j == 0 ? (copy_a ? 2u : 0u) : (copy_a ? 1u : 0u);
         const u32 n_dig = j == 0 ? 0u : beta;
-        const u32 n_key = (j > 0 && i == 0) ? 2u * beta : 0u;
-        mbar_expect_tx(bar, (k_count + n_dig + n_ab + n_key) * RB);
+        mbar_expect_tx(bar, (k_count + n_dig + n_ab) * RB);
         const size_t didx = (size_t)(n1 * j + i) * dstride + (size_t)drow * N;
 #pragma unroll
         for (int kk = 0; kk < K3; kk++)
@@ -313,34 +310,40 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
             tma_load_1d(st + (size_t)(K3 + b) * RUN, a.Dg[i] + b * dig_b + tN + (size_t)srun * RUN, RB, bar);
         if (n_ab >= 1) tma_load_1d(st + (size_t)(K3 + beta) * RUN, a.A[i] + tN + (size_t)srun * RUN, RB, bar);
         if (n_ab == 2) tma_load_1d(st + (size_t)(K3 + beta + 1) * RUN, a.B[i] + tN + (size_t)srun * RUN, RB, bar);
-        if (n_key) {
-            u64* kb = keybuf + (size_t)(j & 1) * 2 * beta * RUN;
-            const u64* ks = a.keys[j] + (size_t)gmod * N + (size_t)run * RUN;
-            for (u32 b = 0; b < beta; b++) {
-                tma_load_1d(kb + (size_t)(2 * b) * RUN, ks + b * key_b, RB, bar);
-                tma_load_1d(kb + (size_t)(2 * b + 1) * RUN, ks + b * key_b + key_c, RB, bar);
-            }
-        }
     };
 
     if (l == 0) {
 #pragma unroll
-        for (int b = 0; b < DM_NS; b++) mbar_init(&full_bar[b], 1);
+        for (int b = 0; b < NS; b++) mbar_init(&full_bar[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
     if (l == 0)
-        for (int p = 0; p < DM_NS - 1; p++) issue(p);
+        for (int p = 0; p < NS - 1; p++) issue(p);
 
     U128 acc0[K3], acc1[K3];
 #pragma unroll
     for (int kk = 0; kk < K3; kk++) acc0[kk] = acc1[kk] = U128{0, 0};
     u32 terms = 0;
-    u32 issued = DM_NS - 1;  // steps the producer has issued (meaningful in thread 0)
+    u32 issued = NS - 1;  // steps the producer has issued (meaningful in thread 0)
     bool failed = false;
+    u64 k0[KB], k1[KB];  // switching-key words of the current giant index at this thread's position
+    u32 pm = 0;          // in-run source position of the middle-layer gather of the current j
 
     for (u32 it = 0; it < n1n2; it++) {
-        const bool ok = mbar_wait_bounded(&full_bar[it % DM_NS], (it / DM_NS) & 1);
+        const u32 j = it / n1, i = it % n1;
+        if (j > 0 && i == 0) {
+            // a new giant index: its key words (not gathered) come straight from
+            // global memory; the loads overlap the wait for the stage below
+            const u64* ks = a.keys[j] + (size_t)gmod * N + s;
+#pragma unroll
+            for (int b = 0; b < KB; b++) {
+                k0[b] = b < (int)beta ? ks[b * key_b] : 0;
+                k1[b] = b < (int)beta ? ks[b * key_b + key_c] : 0;
+            }
+            pm = auto_src(s, a.gal_mid[j], a.log_n) % RUN;
+        }
+        const bool ok = mbar_wait_bounded(&full_bar[it % NS], (it / NS) & 1);
         // everyone has finished step it-1 (its buffer is free) and agrees on success
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -348,11 +351,10 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
         }
         if (l == 0) {
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            issue(it + DM_NS - 1);
-            issued = it + DM_NS;
+            issue(it + NS - 1);
+            issued = it + NS;
         }
-        const u32 j = it / n1, i = it % n1;
-        const u64* st = stage0 + (size_t)(it % DM_NS) * stage_runs * RUN;
+        const u64* st = smem + (size_t)(it % NS) * stage_runs * RUN;
         const bool lifted = (i == 0) && a.lift0;
         u64 av, bv;
         if (j == 0) {
@@ -364,21 +366,23 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
                 bv = st[(K3 + beta + 1) * RUN + l];
             }
         } else {
-            const u32 pm = auto_src(s, a.gal_mid[j], a.log_n) % RUN;
-            const u64* kb = keybuf + (size_t)(j & 1) * 2 * beta * RUN + l;
             U128 x0{0, 0}, x1{0, 0};
-            for (u32 b = 0; b < beta; b++) {
-                const u64 d = st[(K3 + b) * RUN + pm];
-                mac128(x0, d, kb[(2 * b) * RUN]);
-                mac128(x1, d, kb[(2 * b + 1) * RUN]);
+#pragma unroll
+            for (int b = 0; b < KB; b++) {
+                if (b < (int)beta) {
+                    const u64 d = st[(K3 + b) * RUN + pm];
+                    mac128(x0, d, k0[b]);
+                    mac128(x1, d, k1[b]);
+                }
             }
             if (lifted) {
                 if (lift_limb) add128(x0, mul_shoup(st[(K3 + beta) * RUN + pm], lc, lsh, m.q));
             } else {
                 add128(x0, st[(K3 + beta) * RUN + pm]);
             }
-            av = reduce128(x0, m);
-            bv = reduce128(x1, m);
+            // partial reductions (values below 4q < 2^62) are enough to feed the products
+            av = reduce128_lazy(x0, m);
+            bv = reduce128_lazy(x1, m);
         }
 #pragma unroll
         for (int kk = 0; kk < K3; kk++) {
@@ -388,7 +392,7 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
                 mac128(acc1[kk], bv, f);
             }
         }
-        if (++terms == 128) {
+        if (++terms == 64) {  // 64 products below 2^122 each fit the accumulators
             terms = 0;
 #pragma unroll
             for (int kk = 0; kk < K3; kk++) {
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
         // drain: the producer waits (bounded) for every step it issued that was not consumed
         if (l == 0) {
             for (u32 it = 0; it < min(issued, n1n2); it++)
-                mbar_wait_bounded(&full_bar[it % DM_NS], (it / DM_NS) & 1);
+                mbar_wait_bounded(&full_bar[it % NS], (it / NS) & 1);
             atomicExch(a.err, 1u);
         }
         return;
@@ -430,27 +434,27 @@ __global__ void k_wait_selftest(u32* err, u64 limit_ns) {
     if (!ok) atomicExch(err, 1u);
 }
 
-template <int K3, int RUN>
-size_t staged_smem(const DiagMacArgs& a) {
-    const size_t beta = a.n2 > 1 ? a.beta : 0;
-    return 8ull * RUN * (DM_NS * (K3 + beta + 2) + 2 * 2 * beta);
-}
-
 constexpr size_t DM_SMEM_MAX = 226 * 1024;  // dynamic part; the mbarriers take a few static bytes
 
-template <int K3, int RUN>
+template <int K3, int RUN, int NS, int KB>
 bool try_staged(const DiagMacArgs& a, cudaStream_t st) {
-    const size_t sm = staged_smem<K3, RUN>(a);
+    const size_t beta = a.n2 > 1 ? a.beta : 0;
+    const size_t sm = 8ull * RUN * NS * (K3 + beta + 2);
     const u32 N = 1u << a.log_n;
-    if (sm > DM_SMEM_MAX || N % RUN || (a.n2 > 1 && a.beta > 16)) return false;
+    if (sm > DM_SMEM_MAX || N % RUN || beta > (size_t)KB) return false;
     static int attr_ok = -1;
     if (attr_ok < 0)
-        attr_ok = cudaFuncSetAttribute(k_diag_mac_staged<K3, RUN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)DM_SMEM_MAX) == cudaSuccess;
+        attr_ok = cudaFuncSetAttribute(k_diag_mac_staged<K3, RUN, NS, KB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DM_SMEM_MAX) == cudaSuccess;
     if (!attr_ok) return false;
     const dim3 grid(N / RUN, a.ext, (a.n3 + K3 - 1) / K3);
-    k_diag_mac_staged<K3, RUN><<<grid, RUN, sm, st>>>(a);
+    k_diag_mac_staged<K3, RUN, NS, KB><<<grid, RUN, sm, st>>>(a);
     return true;
+}
+
+template <int K3>
+bool launch_staged(const DiagMacArgs& a, cudaStream_t st) {
+    return try_staged<K3, 512, 4, 6>(a, st) || try_staged<K3, 512, 3, 6>(a, st) || try_staged<K3, 256, 4, 6>(a, st);
 }
 
 }  // namespace
@@ -475,10 +479,10 @@ void launch_diag_mac(const DiagMacArgs& a, cudaStream_t st) {
     ProfScope ps(K_DIAG_MAC, st);
     bool done = false;
     switch (k3) {
-        case 1: done = try_staged<1, 512>(a, st) || try_staged<1, 256>(a, st); break;
-        case 2: done = try_staged<2, 512>(a, st) || try_staged<2, 256>(a, st); break;
-        case 4: done = try_staged<4, 512>(a, st) || try_staged<4, 256>(a, st); break;
-        default: done = try_staged<8, 512>(a, st) || try_staged<8, 256>(a, st); break;
+        case 1: done = launch_staged<1>(a, st); break;
+        case 2: done = launch_staged<2>(a, st); break;
+        case 4: done = launch_staged<4>(a, st); break;
+        default: done = launch_staged<8>(a, st); break;
     }
     if (done) {
         count_launch();

@@ -41,9 +41,28 @@ __device__ __forceinline__ u64 mul_shoup(u64 a, u64 w, u64 wp, u64 q) {
     return r >= q ? r - q : r;
 }
 
+// acc += a * b.  The four 32x32 partial products are added into the four
+// 32-bit words of the accumulator along explicit carry chains: ten 32-bit
+// multiply-add instructions, cheaper than the 64-bit mad.lo/madc.hi forms.
+// The caller keeps the 128-bit sum from overflowing.
 __device__ __forceinline__ void mac128(U128& acc, u64 a, u64 b) {
-    asm("mad.lo.cc.u64 %0, %2, %3, %0;\n\t"
-        "madc.hi.u64 %1, %2, %3, %1;"
+    asm("{\n\t.reg .u32 a0, a1, a2, a3, x0, x1, y0, y1;\n\t"
+        "mov.b64 {a0, a1}, %0;\n\t"
+        "mov.b64 {a2, a3}, %1;\n\t"
+        "mov.b64 {x0, x1}, %2;\n\t"
+        "mov.b64 {y0, y1}, %3;\n\t"
+        "mad.lo.cc.u32 a0, x0, y0, a0;\n\t"
+        "madc.hi.cc.u32 a1, x0, y0, a1;\n\t"
+        "madc.lo.cc.u32 a2, x1, y1, a2;\n\t"
+        "madc.hi.u32 a3, x1, y1, a3;\n\t"
+        "mad.lo.cc.u32 a1, x0, y1, a1;\n\t"
+        "madc.hi.cc.u32 a2, x0, y1, a2;\n\t"
+        "addc.u32 a3, a3, 0;\n\t"
+        "mad.lo.cc.u32 a1, x1, y0, a1;\n\t"
+        "madc.hi.cc.u32 a2, x1, y0, a2;\n\t"
+        "addc.u32 a3, a3, 0;\n\t"
+        "mov.b64 %0, {a0, a1};\n\t"
+        "mov.b64 %1, {a2, a3};\n\t}"
         : "+l"(acc.lo), "+l"(acc.hi)
         : "l"(a), "l"(b));
 }
@@ -59,11 +78,13 @@ __device__ __forceinline__ void add128(U128& acc, u64 v) {
 //   qe = x1*m1 + hi(x1*m0) + hi(x0*m1)            (mod 2^64)
 // drops the low partial products, so it is below floor(x/q) by at most 3 and
 // x - qe*q < 4q fits 64 bits.
+__device__ __forceinline__ u64 reduce128_lazy(U128 x, const ModC& m) {  // x mod q up to 3q, in [0, 4q)
+    const u64 qe = x.hi * m.mu_hi + __umul64hi(x.hi, m.mu_lo) + __umul64hi(x.lo, m.mu_hi);
+    return x.lo - qe * m.q;
+}
 __device__ __forceinline__ u64 reduce128(U128 x, const ModC& m) {
-    u64 qe = x.hi * m.mu_hi + __umul64hi(x.hi, m.mu_lo) + __umul64hi(x.lo, m.mu_hi);
-    u64 r = x.lo - qe * m.q;
-    r = r >= m.q ? r - m.q : r;
-    r = r >= m.q ? r - m.q : r;
+    u64 r = reduce128_lazy(x, m);
+    r = r >= 2 * m.q ? r - 2 * m.q : r;
     r = r >= m.q ? r - m.q : r;
     return r;
 }

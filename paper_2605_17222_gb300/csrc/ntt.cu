@@ -135,22 +135,39 @@ __device__ __forceinline__ void tw_at(const ulonglong2* tab, u32 idx, u64& w, u6
     ws = v.y;
 }
 
-// Cooley-Tukey butterfly (forward): (a, b) -> (a + w b, a - w b).
+// Shoup product without the final correction: a w mod q in [0, 2q) for any a < 2^64.
+__device__ __forceinline__ u64 mul_shoup_lazy(u64 a, u64 w, u64 ws, u64 q) {
+    return a * w - __umul64hi(a, ws) * q;
+}
+
+// Cooley-Tukey butterfly (forward), lazy (Harvey): inputs and outputs in
+// [0, 4q) (every modulus is below 2^60, so 4q < 2^64);
+// (a, b) -> (a + w b, a - w b) mod q up to multiples of q.
 __device__ __forceinline__ void ct_bfly(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
     u64 w, ws;
     tw_at(tab, idx, w, ws);
-    const u64 v = mul_shoup(b, w, ws, q);
-    b = sub_mod(a, v, q);
-    a = add_mod(a, v, q);
+    const u64 q2 = 2 * q;
+    const u64 x = a >= q2 ? a - q2 : a;
+    const u64 v = mul_shoup_lazy(b, w, ws, q);
+    a = x + v;
+    b = x - v + q2;
 }
 
-// Gentleman-Sande butterfly (inverse): (a, b) -> (a + b, (a - b) w).
+// Gentleman-Sande butterfly (inverse), lazy: inputs and outputs in [0, 2q);
+// (a, b) -> (a + b, (a - b) w) mod q up to multiples of q.
 __device__ __forceinline__ void gs_bfly(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
     u64 w, ws;
     tw_at(tab, idx, w, ws);
-    const u64 s = add_mod(a, b, q);
-    b = mul_shoup(sub_mod(a, b, q), w, ws, q);
-    a = s;
+    const u64 q2 = 2 * q;
+    const u64 s = a + b;
+    b = mul_shoup_lazy(a - b + q2, w, ws, q);
+    a = s >= q2 ? s - q2 : s;
+}
+
+// [0, 4q) -> [0, q)
+__device__ __forceinline__ u64 canon4(u64 x, u64 q) {
+    x = x >= 2 * q ? x - 2 * q : x;
+    return x >= q ? x - q : x;
 }
 
 // Every pass works on "lines" of S = 2^LOGS words (a column of the R x C
@@ -169,7 +186,7 @@ __device__ __forceinline__ u32 pad16(u32 i) { return i + (i >> 4); }
 // ------------------------------------------------------------------ forward, column pass
 // Global stages 0..LOGS-1 (m = 2^ss, twiddle psi^brv(m + r / 2t_r)).
 template <int LOGS, bool BCONV>
-__global__ void __launch_bounds__(THREADS) k_fwd_cols(const __grid_constant__ NttTables T,
+__global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<FwdJob> jobs) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
     __shared__ u64 sm[S * W];
@@ -181,16 +198,23 @@ __global__ void __launch_bounds__(THREADS) k_fwd_cols(const __grid_constant__ Nt
     const u64 q = m.q;
     const ulonglong2* tw = T.psi + (size_t)J.mod * N;
     u64 x[16];
-#pragma unroll
-    for (int v = 0; v < 16; v++) {
-        const size_t gi = (size_t)(u + TPL * v) * C + col;
-        if constexpr (BCONV) {
+    if constexpr (BCONV) {
+        // basis conversion (Eq. 3) of the thread's 16 words, staged through its
+        // own slots of the exchange buffer so that this part stays a compact loop
+        const u64* bc = J.bcst;
+        const u32 ns = J.nsrc;
+#pragma unroll 4
+        for (int v = 0; v < 16; v++) {
+            const u64* src = J.src + (size_t)(u + TPL * v) * C + col;
             U128 acc{0, 0};
-            for (u32 j = 0; j < J.nsrc; j++) mac128(acc, J.src[(size_t)j * N + gi], J.bcst[j]);
-            x[v] = reduce128(acc, m);
-        } else {
-            x[v] = J.src[gi];
+            for (u32 j = 0; j < ns; j++) mac128(acc, src[(size_t)j * N], bc[j]);
+            sm[(u + TPL * v) * W + c] = reduce128(acc, m);
         }
+#pragma unroll
+        for (int v = 0; v < 16; v++) x[v] = sm[(u + TPL * v) * W + c];
+    } else {
+#pragma unroll
+        for (int v = 0; v < 16; v++) x[v] = J.src[(size_t)(u + TPL * v) * C + col];
     }
 #pragma unroll
     for (int ss = 0; ss < 4; ss++) {
@@ -218,7 +242,7 @@ __global__ void __launch_bounds__(THREADS) k_fwd_cols(const __grid_constant__ Nt
 // ------------------------------------------------------------------ forward, row pass
 // Global stages log_r..log_n-1 (m = 2^(log_r+ss), twiddle psi^brv(m + row 2^ss + x / 2t)).
 template <int LOGS, bool SUBMUL>
-__global__ void __launch_bounds__(THREADS) k_fwd_rows(const __grid_constant__ NttTables T,
+__global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<FwdJob> jobs) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
     __shared__ u64 sm[B * SP];
@@ -261,7 +285,7 @@ __global__ void __launch_bounds__(THREADS) k_fwd_rows(const __grid_constant__ Nt
 #pragma unroll
     for (int v = 0; v < 16; v++) {
         const u32 xi = u + TPL * v;
-        const u64 val = sr[pad16(xi)];
+        const u64 val = canon4(sr[pad16(xi)], q);
         if constexpr (SUBMUL) {
             J.subout[base + xi] = mul_shoup(sub_mod(J.subx[base + xi], val, q), J.c, J.c_sh, q);
         } else {
@@ -273,7 +297,7 @@ __global__ void __launch_bounds__(THREADS) k_fwd_rows(const __grid_constant__ Nt
 // ------------------------------------------------------------------ inverse, row pass
 // GS stages with half-width t = 1..S/2 (m = N/2t, twiddle psi^-brv(m + row S/2t + x/2t)).
 template <int LOGS, bool GATHER>
-__global__ void __launch_bounds__(THREADS) k_inv_rows(const __grid_constant__ NttTables T,
+__global__ void __launch_bounds__(THREADS, 4) k_inv_rows(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<InvJob> jobs) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
     __shared__ u64 sm[B * SP];
@@ -327,7 +351,7 @@ __global__ void __launch_bounds__(THREADS) k_inv_rows(const __grid_constant__ Nt
 // GS stages with half-width C*t_r, t_r = 1..S/2 (m = S/2t_r, twiddle psi^-brv(m + r/2t_r)),
 // then the scaling by c (N^-1 and any per-limb constant).
 template <int LOGS>
-__global__ void __launch_bounds__(THREADS) k_inv_cols(const __grid_constant__ NttTables T,
+__global__ void __launch_bounds__(THREADS, 4) k_inv_cols(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<InvJob> jobs) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
     __shared__ u64 sm[S * W];
