@@ -289,71 +289,109 @@ struct Arena {
 };
 
 // ------------------------------------------------------------------ key switching steps
-// Decompose (Fig. 1, Eq. 3): c [level][N] (gathered through x -> x^gal if gal)
-// -> digits [beta][level+K][N].  Y: scratch [level][N].
-void op_decompose(ckks_ctx* C, u32 level, const u64* c, u32 gal, u64* digits, u64* Y, cudaStream_t st) {
+// Decompose (Fig. 1, Eq. 3) of `count` polynomials at once: c_i [level][N]
+// (gathered through x -> x^gal if gal) -> digits_i [beta][level+K][N].
+// Y: scratch [count][level][N].  One launch pair per transform direction
+// covers every polynomial, so small steps still fill the GPU.
+void op_decompose_batch(ckks_ctx* C, u32 level, const std::vector<const u64*>& cs, u32 gal,
+                        const std::vector<u64*>& digits, u64* Y, cudaStream_t st) {
     const LevelConsts& LC = C->lc(level);
     const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
-    std::vector<InvJob> ij(level);
-    for (u32 j = 0; j < level; j++)
-        ij[j] = InvJob{c + (size_t)j * N, Y + (size_t)j * N, Y + (size_t)j * N, LC.dec_c[j], LC.dec_sh[j], j, gal};
-    launch_inv_ntt(C->T, ij.data(), level, st);
+    const u32 cnt = (u32)cs.size();
+    std::vector<InvJob> ij;
+    ij.reserve((size_t)cnt * level);
+    for (u32 p = 0; p < cnt; p++) {
+        u64* Yp = Y + (size_t)p * level * N;
+        for (u32 j = 0; j < level; j++)
+            ij.push_back(InvJob{cs[p] + (size_t)j * N, Yp + (size_t)j * N, Yp + (size_t)j * N, LC.dec_c[j], LC.dec_sh[j],
+                                j, gal});
+    }
+    launch_inv_ntt(C->T, ij.data(), (int)ij.size(), st);
     std::vector<FwdJob> fj;
-    for (u32 b = 0; b < beta; b++) {
-        const u32 first = b * C->alpha, cnt = std::min(C->alpha, level - first);
-        for (u32 t = 0; t < ext; t++) {
-            if (t >= first && t < first + cnt) continue;
-            fj.push_back(FwdJob{Y + (size_t)first * N, digits + ((size_t)b * ext + t) * N,
-                                LC.dec_tab + ((size_t)b * ext + t) * C->alpha, nullptr, nullptr, 0, 0,
-                                C->gmod(level, t), cnt});
+    for (u32 p = 0; p < cnt; p++) {
+        u64* Yp = Y + (size_t)p * level * N;
+        for (u32 b = 0; b < beta; b++) {
+            const u32 first = b * C->alpha, n = std::min(C->alpha, level - first);
+            for (u32 t = 0; t < ext; t++) {
+                if (t >= first && t < first + n) continue;
+                fj.push_back(FwdJob{Yp + (size_t)first * N, digits[p] + ((size_t)b * ext + t) * N,
+                                    LC.dec_tab + ((size_t)b * ext + t) * C->alpha, nullptr, nullptr, 0, 0,
+                                    C->gmod(level, t), n});
+            }
         }
     }
     launch_fwd_ntt(C->T, fj.data(), (int)fj.size(), st);
-    for (u32 b = 0; b < beta; b++) {
-        const u32 first = b * C->alpha, cnt = std::min(C->alpha, level - first);
-        u64* dst = digits + ((size_t)b * ext + first) * N;
-        if (gal) launch_automorphism(c + (size_t)first * N, dst, cnt, gal, C->log_n, st);
-        else CK(cudaMemcpyAsync(dst, c + (size_t)first * N, (size_t)cnt * N * 8, cudaMemcpyDeviceToDevice, st));
-    }
+    for (u32 p = 0; p < cnt; p++)
+        for (u32 b = 0; b < beta; b++) {
+            const u32 first = b * C->alpha, n = std::min(C->alpha, level - first);
+            u64* dst = digits[p] + ((size_t)b * ext + first) * N;
+            if (gal) launch_automorphism(cs[p] + (size_t)first * N, dst, n, gal, C->log_n, st);
+            else CK(cudaMemcpyAsync(dst, cs[p] + (size_t)first * N, (size_t)n * N * 8, cudaMemcpyDeviceToDevice, st));
+        }
 }
 
-// Modulus switch down over a contiguous source run of x: INTT the sources
-// (scaled), basis-convert to the targets 0..ntgt-1 fused into the forward NTT,
-// and finish with out = (x_j - conv_j) * inv_j (Eq. 4 / Eq. 1).
-void op_down(ckks_ctx* C, u32 level, const u64* x, u32 src_first, const std::vector<u32>& src_g,
-             const std::vector<u64>& sc, const std::vector<u64>& ssh, const u64* tab, u32 ntgt,
-             const std::vector<u64>& inv, const std::vector<u64>& inv_sh, u64* out, u64* Y, cudaStream_t st) {
-    const u32 N = C->N, ns = (u32)src_g.size();
-    std::vector<InvJob> ij(ns);
-    for (u32 i = 0; i < ns; i++)
-        ij[i] = InvJob{x + (size_t)(src_first + i) * N, Y + (size_t)i * N, Y + (size_t)i * N, sc[i], ssh[i], src_g[i], 0};
-    launch_inv_ntt(C->T, ij.data(), ns, st);
-    std::vector<FwdJob> fj(ntgt);
-    for (u32 j = 0; j < ntgt; j++)
-        fj[j] = FwdJob{Y, out + (size_t)j * N, tab + (size_t)j * ns, x + (size_t)j * N, out + (size_t)j * N,
-                       inv[j], inv_sh[j], j, ns};
-    launch_fwd_ntt(C->T, fj.data(), (int)ntgt, st);
+void op_decompose(ckks_ctx* C, u32 level, const u64* c, u32 gal, u64* digits, u64* Y, cudaStream_t st) {
+    op_decompose_batch(C, level, std::vector<const u64*>{c}, gal, std::vector<u64*>{digits}, Y, st);
 }
 
-void op_moddown(ckks_ctx* C, u32 level, const u64* x, u64* out, u64* Y, cudaStream_t st) {
+// Modulus switch down of `count` polynomials over a contiguous source run:
+// INTT the sources (scaled), basis-convert to the targets 0..ntgt-1 fused into
+// the forward NTT, and finish with out = (x_j - conv_j) * inv_j (Eq. 4 / Eq. 1).
+// Y: scratch [count][ns][N].
+void op_down_batch(ckks_ctx* C, const std::vector<const u64*>& xs, u32 src_first, const std::vector<u32>& src_g,
+                   const std::vector<u64>& sc, const std::vector<u64>& ssh, const u64* tab, u32 ntgt,
+                   const std::vector<u64>& inv, const std::vector<u64>& inv_sh, const std::vector<u64*>& outs, u64* Y,
+                   cudaStream_t st) {
+    const u32 N = C->N, ns = (u32)src_g.size(), cnt = (u32)xs.size();
+    std::vector<InvJob> ij;
+    for (u32 p = 0; p < cnt; p++)
+        for (u32 i = 0; i < ns; i++) {
+            u64* y = Y + ((size_t)p * ns + i) * N;
+            ij.push_back(InvJob{xs[p] + (size_t)(src_first + i) * N, y, y, sc[i], ssh[i], src_g[i], 0});
+        }
+    launch_inv_ntt(C->T, ij.data(), (int)ij.size(), st);
+    std::vector<FwdJob> fj;
+    for (u32 p = 0; p < cnt; p++)
+        for (u32 j = 0; j < ntgt; j++)
+            fj.push_back(FwdJob{Y + (size_t)p * ns * N, outs[p] + (size_t)j * N, tab + (size_t)j * ns,
+                                xs[p] + (size_t)j * N, outs[p] + (size_t)j * N, inv[j], inv_sh[j], j, ns});
+    launch_fwd_ntt(C->T, fj.data(), (int)fj.size(), st);
+}
+
+void op_moddown_batch(ckks_ctx* C, u32 level, const std::vector<const u64*>& xs, const std::vector<u64*>& outs,
+                      u64* Y, cudaStream_t st) {
     const LevelConsts& LC = C->lc(level);
     std::vector<u32> g;
     for (u32 i = 0; i < C->K; i++) g.push_back(C->L + i);
-    op_down(C, level, x, level, g, LC.md_c, LC.md_sh, LC.md_tab, level, LC.md_pinv, LC.md_pinv_sh, out, Y, st);
+    op_down_batch(C, xs, level, g, LC.md_c, LC.md_sh, LC.md_tab, level, LC.md_pinv, LC.md_pinv_sh, outs, Y, st);
 }
 
-void op_moddown_rescale(ckks_ctx* C, u32 level, const u64* x, u64* out, u64* Y, cudaStream_t st) {
+void op_moddown(ckks_ctx* C, u32 level, const u64* x, u64* out, u64* Y, cudaStream_t st) {
+    op_moddown_batch(C, level, std::vector<const u64*>{x}, std::vector<u64*>{out}, Y, st);
+}
+
+void op_moddown_rescale_batch(ckks_ctx* C, u32 level, const std::vector<const u64*>& xs,
+                              const std::vector<u64*>& outs, u64* Y, cudaStream_t st) {
     const LevelConsts& LC = C->lc(level);
     std::vector<u32> g{level - 1};
     for (u32 i = 0; i < C->K; i++) g.push_back(C->L + i);
-    op_down(C, level, x, level - 1, g, LC.mdr_c, LC.mdr_sh, LC.mdr_tab, level - 1, LC.mdr_pinv, LC.mdr_pinv_sh, out,
-            Y, st);
+    op_down_batch(C, xs, level - 1, g, LC.mdr_c, LC.mdr_sh, LC.mdr_tab, level - 1, LC.mdr_pinv, LC.mdr_pinv_sh, outs,
+                  Y, st);
+}
+
+void op_moddown_rescale(ckks_ctx* C, u32 level, const u64* x, u64* out, u64* Y, cudaStream_t st) {
+    op_moddown_rescale_batch(C, level, std::vector<const u64*>{x}, std::vector<u64*>{out}, Y, st);
+}
+
+void op_rescale_batch(ckks_ctx* C, u32 level, const std::vector<const u64*>& xs, const std::vector<u64*>& outs,
+                      u64* Y, cudaStream_t st) {
+    const LevelConsts& LC = C->lc(level);
+    op_down_batch(C, xs, level - 1, std::vector<u32>{level - 1}, LC.rs_c, LC.rs_sh, LC.rs_tab, level - 1, LC.rs_inv,
+                  LC.rs_inv_sh, outs, Y, st);
 }
 
 void op_rescale(ckks_ctx* C, u32 level, const u64* x, u64* out, u64* Y, cudaStream_t st) {
-    const LevelConsts& LC = C->lc(level);
-    op_down(C, level, x, level - 1, std::vector<u32>{level - 1}, LC.rs_c, LC.rs_sh, LC.rs_tab, level - 1, LC.rs_inv,
-            LC.rs_inv_sh, out, Y, st);
+    op_rescale_batch(C, level, std::vector<const u64*>{x}, std::vector<u64*>{out}, Y, st);
 }
 
 const u64* key_of(ckks_ctx* C, int64_t r) {
@@ -428,21 +466,29 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
     const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
     const int64_t s = f->stride;
     Arena ar(st, N);
-    u64* Y = ar.limbs(std::max(level, C->K + 1));
+    const u32 nb = std::max<u32>(1, std::max(n1 - 1, n3 - 1));  // widest batch of the key-switch phases
+    u64* Y = ar.limbs(std::max<size_t>((size_t)nb * level, 2 * (C->K + 1)));
     std::vector<u64*> A(n1, nullptr), B(n1, nullptr), Dg(n1, nullptr);
     Dg[0] = ar.limbs((size_t)beta * ext);
     op_decompose(C, level, io.c1, 0, Dg[0], Y, st);  // line 1
-    u64* Tq = (n1 > 1 || n3 > 1) ? ar.limbs(level) : nullptr;
-    for (u32 i = 1; i < n1; i++) {  // lines 3-7
+    for (u32 i = 1; i < n1; i++) {                     // lines 2-5 (the lift is fused)
         const int64_t r = s * i;
         A[i] = ar.limbs(ext);
         B[i] = ar.limbs(ext);
         op_ks_inner(C, level, Dg[0], key_of(C, r), C->galois(r), io.c0, 2, A[i], B[i], 0, st);
-        if (n2 > 1) {
+    }
+    if (n2 > 1 && n1 > 1) {  // lines 6-7 for every i at once
+        std::vector<const u64*> bs, tqc;
+        std::vector<u64*> tq, dg;
+        for (u32 i = 1; i < n1; i++) {
+            bs.push_back(B[i]);
+            tq.push_back(ar.limbs(level));
+            tqc.push_back(tq.back());
             Dg[i] = ar.limbs((size_t)beta * ext);
-            op_moddown(C, level, B[i], Tq, Y, st);
-            op_decompose(C, level, Tq, 0, Dg[i], Y, st);
+            dg.push_back(Dg[i]);
         }
+        op_moddown_batch(C, level, bs, tq, Y, st);
+        op_decompose_batch(C, level, tqc, 0, dg, Y, st);
     }
     DiagMacArgs a = dm_base(C, level, true, f);
     a.n1 = n1;
@@ -466,15 +512,42 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
         a.gal_diag[k] = k ? C->galois(-s * n1 * n2 * k) : 0;
     }
     launch_diag_mac(a, st);  // lines 8-14
-    u64* Dk = n3 > 1 ? ar.limbs((size_t)beta * ext) : nullptr;
-    for (u32 k = 1; k < n3; k++) {  // lines 15-18
-        const int64_t r = s * n1 * n2 * k;
-        op_moddown(C, level, U1[k], Tq, Y, st);
-        op_decompose(C, level, Tq, 0, Dk, Y, st);
-        op_ks_inner(C, level, Dk, key_of(C, r), C->galois(r), U0[k], 1, U0[0], U1[0], 1, st);
+    if (n3 > 1) {            // lines 15-18 for every k at once
+        std::vector<const u64*> us, tqc;
+        std::vector<u64*> tq, dk;
+        for (u32 k = 1; k < n3; k++) {
+            us.push_back(U1[k]);
+            tq.push_back(ar.limbs(level));
+            tqc.push_back(tq.back());
+            dk.push_back(ar.limbs((size_t)beta * ext));
+        }
+        op_moddown_batch(C, level, us, tq, Y, st);
+        op_decompose_batch(C, level, tqc, 0, dk, Y, st);
+        for (u32 k0 = 1; k0 < n3; k0 += KS_MAX_MULTI) {
+            KsMultiArgs m;
+            memset(&m, 0, sizeof(m));
+            m.count = std::min<u32>(KS_MAX_MULTI, n3 - k0);
+            for (u32 c = 0; c < m.count; c++) {
+                const u32 k = k0 + c;
+                const int64_t r = s * n1 * n2 * k;
+                m.digits[c] = dk[k - 1];
+                m.keys[c] = key_of(C, r);
+                m.x0[c] = U0[k];
+                m.gal[c] = C->galois(r);
+            }
+            m.out0 = U0[0];
+            m.out1 = U1[0];
+            m.mods = (const ModC*)C->d_mods.p;
+            m.level = level;
+            m.ext = ext;
+            m.L = C->L;
+            m.beta = beta;
+            m.log_n = C->log_n;
+            launch_ks_multi(m, st);
+        }
     }
-    op_moddown_rescale(C, level, U0[0], io.o0, Y, st);  // line 19
-    op_moddown_rescale(C, level, U1[0], io.o1, Y, st);
+    op_moddown_rescale_batch(C, level, std::vector<const u64*>{U0[0], U1[0]}, std::vector<u64*>{io.o0, io.o1}, Y,
+                             st);  // line 19
 }
 
 // BSGS, Eq. (5): un-hoisted rotations (each with its own Decompose of the

@@ -76,6 +76,22 @@ struct KsArgs {
 };
 void launch_ks_inner(const KsArgs& a, cudaStream_t st);
 
+// out_c += sum_k phi_{r_k}(x0_k (c = 0 only) + <D_k, swk~_{r_k, c}>), k < count:
+// the outer key-switch layer of Algorithm 2 (lines 17-18) for every giant
+// index at once.
+constexpr int KS_MAX_MULTI = 64;
+struct KsMultiArgs {
+    const u64* digits[KS_MAX_MULTI];  // [beta][ext][N] each
+    const u64* keys[KS_MAX_MULTI];    // [beta_max][2][L+k][N] each
+    const u64* x0[KS_MAX_MULTI];      // [ext][N] each
+    u32 gal[KS_MAX_MULTI];
+    u64* out0;
+    u64* out1;
+    const ModC* mods;
+    u32 count, level, ext, L, beta, log_n;
+};
+void launch_ks_multi(const KsMultiArgs& a, cudaStream_t st);
+
 // Multi-output plaintext-diagonal multiply-accumulate with the middle
 // (hoisted) key-switch layer fused in (K6).  See ks.cu.
 constexpr int DM_MAX_N1 = 64;

@@ -53,6 +53,36 @@ __global__ void __launch_bounds__(THREADS) k_ks_inner(const __grid_constant__ Ks
     a.out1[o] = r1;
 }
 
+// ------------------------------------------------------------------ K4, all giant indices at once
+__global__ void __launch_bounds__(THREADS) k_ks_multi(const __grid_constant__ KsMultiArgs a) {
+    const u32 N = 1u << a.log_n;
+    const u32 s = blockIdx.x * THREADS + threadIdx.x;
+    const u32 t = blockIdx.y;
+    if (s >= N) return;
+    const u32 kp = a.ext - a.level;
+    const u32 gmod = t < a.level ? t : a.L + (t - a.level);
+    const ModC m = a.mods[gmod];
+    const size_t key_b = 2ull * (a.L + kp) * N, key_c = (size_t)(a.L + kp) * N;
+    const size_t o = (size_t)t * N + s;
+    U128 acc0{a.out0[o], 0}, acc1{a.out1[o], 0};
+    for (u32 k = 0; k < a.count; k++) {
+        const u32 src = auto_src(s, a.gal[k], a.log_n);
+        const u64* D = a.digits[k] + (size_t)t * N + src;
+        const u64* K = a.keys[k] + (size_t)gmod * N + s;
+        add128(acc0, a.x0[k][(size_t)t * N + src]);
+        for (u32 b = 0; b < a.beta; b++) {
+            const u64 d = D[(size_t)b * a.ext * N];
+            mac128(acc0, d, K[b * key_b]);
+            mac128(acc1, d, K[b * key_b + key_c]);
+        }
+        // keep the running sums bounded: one partial reduction per giant index
+        acc0 = U128{reduce128_lazy(acc0, m), 0};
+        acc1 = U128{reduce128_lazy(acc1, m), 0};
+    }
+    a.out0[o] = reduce128(acc0, m);
+    a.out1[o] = reduce128(acc1, m);
+}
+
 // ------------------------------------------------------------------ K6
 // For one word s of limb t and K3 giant indices k (a chunk of the n3 outer
 // rotations) this computes
@@ -200,7 +230,6 @@ __global__ void __launch_bounds__(THREADS, 2) k_diag_mac(const __grid_constant__
 // leaves the loop together (the decision goes through __syncthreads_or); the
 // producer then waits, bounded again, for the copies it has in flight before
 // the CTA exits.
-constexpr int DM_NS = 2;                              // stage ring depth
 constexpr u64 DM_WAIT_NS = 1000000000ull;              // a wait gives up after 1 s
 
 __device__ __forceinline__ u64 global_ns() {
@@ -461,6 +490,13 @@ bool launch_staged(const DiagMacArgs& a, cudaStream_t st) {
 
 void launch_wait_selftest(u32* err, u64 limit_ns, cudaStream_t st) {
     k_wait_selftest<<<1, 32, 0, st>>>(err, limit_ns);
+    count_launch();
+}
+
+void launch_ks_multi(const KsMultiArgs& a, cudaStream_t st) {
+    const u32 N = 1u << a.log_n;
+    ProfScope ps(K_KS_INNER, st);
+    k_ks_multi<<<dim3((N + THREADS - 1) / THREADS, a.ext), THREADS, 0, st>>>(a);
     count_launch();
 }
 

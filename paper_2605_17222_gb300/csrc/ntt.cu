@@ -120,7 +120,7 @@ ProfScope::~ProfScope() {
 
 namespace {
 
-constexpr int MAXJ = 96;
+constexpr int MAXJ = 240;  // jobs per launch (kernel parameters are passed by value)
 constexpr int THREADS = 256;
 
 template <typename J>
