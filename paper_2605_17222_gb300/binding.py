@@ -46,11 +46,12 @@ def declared_functions() -> list:
 
 
 def lib():
-    """Load the library, building it first if the sources are newer."""
+    """Load the library, building it first if the sources are newer
+    (CKKS_LT_LIBRARY names a prebuilt copy to load instead)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build()
+    path = os.environ.get("CKKS_LT_LIBRARY") or _build.build()
     L = ctypes.CDLL(path)
     P, U32, I32, SZ, I = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_size_t, ctypes.c_int
     PP = ctypes.POINTER(ctypes.c_void_p)
