@@ -447,6 +447,7 @@ DiagMacArgs dm_base(ckks_ctx* C, u32 level, bool with_p, const ckks_diags* f) {
     a.log_n = C->log_n;
     a.diag_level = f->level;
     a.err = (u32*)C->d_err.p;
+    a.batch = 1;
     return a;
 }
 
@@ -497,6 +498,8 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
     a.lift0 = 1;
     a.A[0] = io.c0;
     a.B[0] = io.c1;
+    a.c0[0] = io.c0;
+    a.c1[0] = io.c1;
     for (u32 i = 1; i < n1; i++) a.A[i] = A[i], a.B[i] = B[i];
     for (u32 i = 0; i < n1; i++) a.Dg[i] = Dg[i];
     for (u32 j = 1; j < n2; j++) {
@@ -548,6 +551,140 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
     }
     op_moddown_rescale_batch(C, level, std::vector<const u64*>{U0[0], U1[0]}, std::vector<u64*>{io.o0, io.o1}, Y,
                              st);  // line 19
+}
+
+// TH-BSGS (and its DH / diagonal special cases) for a batch of ciphertexts at
+// one level that share the diagonals, the keys and the split.  Every step runs
+// once for the whole batch: the Decompose/ModDown launches take every
+// ciphertext's limbs, the inner-layer key products go out as one launch with
+// the ciphertexts of each key adjacent, and K6 runs with a batch dimension so
+// that each diagonal and key word is fetched from HBM once for the batch.
+// The results are identical to per-ciphertext sched_th.
+void sched_th_batch(ckks_ctx* C, u32 level, const std::vector<LtIO>& ios, const ckks_diags* f, u32 n1, u32 n2,
+                    u32 n3, cudaStream_t st) {
+    const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
+    const u32 nbat = (u32)ios.size();
+    const size_t dig = (size_t)beta * ext;  // limbs of one digit set
+    const int64_t s = f->stride;
+    Arena ar(st, N);
+    const u32 nb = std::max<u32>(1, std::max(n1 - 1, n3 - 1)) * nbat;
+    u64* Y = ar.limbs(std::max<size_t>((size_t)std::max(nb, nbat) * level, 2ull * nbat * (C->K + 1)));
+    u64* Aall = ar.limbs((size_t)nbat * n1 * ext);  // [b][i][ext]; i = 0 unused (lifted input)
+    u64* Ball = ar.limbs((size_t)nbat * n1 * ext);
+    u64* Dall = ar.limbs((size_t)nbat * n1 * dig);  // [b][i][beta][ext]
+    u64* Uall = ar.limbs((size_t)nbat * n3 * 2 * ext);  // [b][k][c][ext]
+    auto Ap = [&](u32 b, u32 i) { return Aall + ((size_t)b * n1 + i) * ext * N; };
+    auto Bp = [&](u32 b, u32 i) { return Ball + ((size_t)b * n1 + i) * ext * N; };
+    auto Dp = [&](u32 b, u32 i) { return Dall + ((size_t)b * n1 + i) * dig * N; };
+    auto Up = [&](u32 b, u32 k, u32 c) { return Uall + (((size_t)b * n3 + k) * 2 + c) * ext * N; };
+    {  // line 1
+        std::vector<const u64*> cs;
+        std::vector<u64*> ds;
+        for (u32 b = 0; b < nbat; b++) cs.push_back(ios[b].c1), ds.push_back(Dp(b, 0));
+        op_decompose_batch(C, level, cs, 0, ds, Y, st);
+    }
+    if (n1 > 1) {  // lines 2-5, every (i, b) in launches of KS_MAX_BATCH products
+        std::vector<KsBatchEntry> es;
+        for (u32 i = 1; i < n1; i++)
+            for (u32 b = 0; b < nbat; b++) {
+                const int64_t r = s * i;
+                es.push_back(KsBatchEntry{Dp(b, 0), key_of(C, r), ios[b].c0, Ap(b, i), Bp(b, i), C->galois(r), 0});
+            }
+        for (size_t e0 = 0; e0 < es.size(); e0 += KS_MAX_BATCH) {
+            KsBatchArgs k;
+            memset(&k, 0, sizeof(k));
+            k.count = (u32)std::min<size_t>(KS_MAX_BATCH, es.size() - e0);
+            for (u32 c = 0; c < k.count; c++) k.e[c] = es[e0 + c];
+            k.mods = (const ModC*)C->d_mods.p;
+            k.lift_c = C->d_lift.p;
+            k.lift_sh = C->d_lift_sh.p;
+            k.level = level;
+            k.ext = ext;
+            k.L = C->L;
+            k.beta = beta;
+            k.log_n = C->log_n;
+            launch_ks_batch(k, st);
+        }
+    }
+    if (n2 > 1 && n1 > 1) {  // lines 6-7
+        std::vector<const u64*> bs, tqc;
+        std::vector<u64*> tq, dg;
+        for (u32 b = 0; b < nbat; b++)
+            for (u32 i = 1; i < n1; i++) {
+                bs.push_back(Bp(b, i));
+                tq.push_back(ar.limbs(level));
+                tqc.push_back(tq.back());
+                dg.push_back(Dp(b, i));
+            }
+        op_moddown_batch(C, level, bs, tq, Y, st);
+        op_decompose_batch(C, level, tqc, 0, dg, Y, st);
+    }
+    DiagMacArgs a = dm_base(C, level, true, f);
+    a.n1 = n1;
+    a.n2 = n2;
+    a.n3 = n3;
+    a.lift0 = 1;
+    a.batch = nbat;
+    for (u32 b = 0; b < nbat; b++) a.c0[b] = ios[b].c0, a.c1[b] = ios[b].c1;
+    for (u32 i = 0; i < n1; i++) a.A[i] = Ap(0, i), a.B[i] = Bp(0, i), a.Dg[i] = Dp(0, i);
+    a.bs_ab = (u64)n1 * ext * N;
+    a.bs_dg = (u64)n1 * dig * N;
+    a.bs_u = (u64)n3 * 2 * ext * N;
+    for (u32 j = 1; j < n2; j++) {
+        a.keys[j] = key_of(C, s * n1 * j);
+        a.gal_mid[j] = C->galois(s * n1 * j);
+    }
+    for (u32 k = 0; k < n3; k++) {
+        a.U0[k] = Up(0, k, 0);
+        a.U1[k] = Up(0, k, 1);
+        a.gal_diag[k] = k ? C->galois(-s * n1 * n2 * k) : 0;
+    }
+    launch_diag_mac(a, st);  // lines 8-14
+    if (n3 > 1) {            // lines 15-18
+        std::vector<const u64*> us, tqc;
+        std::vector<u64*> tq, dk;
+        for (u32 b = 0; b < nbat; b++)
+            for (u32 k = 1; k < n3; k++) {
+                us.push_back(Up(b, k, 1));
+                tq.push_back(ar.limbs(level));
+                tqc.push_back(tq.back());
+                dk.push_back(ar.limbs(dig));
+            }
+        op_moddown_batch(C, level, us, tq, Y, st);
+        op_decompose_batch(C, level, tqc, 0, dk, Y, st);
+        for (u32 b = 0; b < nbat; b++)
+            for (u32 k0 = 1; k0 < n3; k0 += KS_MAX_MULTI) {
+                KsMultiArgs m;
+                memset(&m, 0, sizeof(m));
+                m.count = std::min<u32>(KS_MAX_MULTI, n3 - k0);
+                for (u32 c = 0; c < m.count; c++) {
+                    const u32 k = k0 + c;
+                    const int64_t r = s * n1 * n2 * k;
+                    m.digits[c] = dk[(size_t)b * (n3 - 1) + (k - 1)];
+                    m.keys[c] = key_of(C, r);
+                    m.x0[c] = Up(b, k, 0);
+                    m.gal[c] = C->galois(r);
+                }
+                m.out0 = Up(b, 0, 0);
+                m.out1 = Up(b, 0, 1);
+                m.mods = (const ModC*)C->d_mods.p;
+                m.level = level;
+                m.ext = ext;
+                m.L = C->L;
+                m.beta = beta;
+                m.log_n = C->log_n;
+                launch_ks_multi(m, st);
+            }
+    }
+    std::vector<const u64*> xs;
+    std::vector<u64*> outs;
+    for (u32 b = 0; b < nbat; b++) {
+        xs.push_back(Up(b, 0, 0));
+        outs.push_back(ios[b].o0);
+        xs.push_back(Up(b, 0, 1));
+        outs.push_back(ios[b].o1);
+    }
+    op_moddown_rescale_batch(C, level, xs, outs, Y, st);  // line 19
 }
 
 // BSGS, Eq. (5): un-hoisted rotations (each with its own Decompose of the
@@ -1061,13 +1198,69 @@ ckks_status lt_eval(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_al
     return guarded([&] { lt_eval_impl(ctx, in, f, algo, split, out, (cudaStream_t)stream, chosen); });
 }
 
+// Validates one LT of a batch and returns its split (as lt_eval would choose it).
+static lt_split batch_item_split(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_algo algo,
+                                 const lt_split* split, const ckks_ct* out) {
+    if (!in || !f || !out) fail(CKKS_EINVAL, "null argument");
+    if (in->ctx != ctx || f->ctx != ctx || out->ctx != ctx) fail(CKKS_EINVAL, "objects of another context");
+    const u32 level = in->level;
+    if (level < 2 || level > f->level || out->level != level - 1) fail(CKKS_EINVAL, "bad levels in the batch");
+    if (out->d == in->d) fail(CKKS_EINVAL, "output must not alias input");
+    const u32 D = f->n_diag;
+    lt_split sp = (split && (split->n1 || split->n2 || split->n3)) ? *split : choose_split(ctx, algo, level, D);
+    if (algo == LT_DIAG) sp = lt_split{1, D, 1};
+    if (algo != LT_TH_BSGS && sp.n3 == 0) sp.n3 = 1;
+    validate_split(algo, D, sp);
+    for (int64_t r : rotations(algo, sp, D)) key_of(ctx, r * f->stride);
+    return sp;
+}
+
 ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* in, const ckks_diags* const* f,
                           const lt_algo* algos, const lt_split* splits, ckks_ct* const* out, void* stream) {
     return guarded([&] {
         if (!ctx || (count && (!in || !f || !out))) fail(CKKS_EINVAL, "null argument");
-        for (u32 i = 0; i < count; i++)
-            lt_eval_impl(ctx, in[i], f[i], algos ? algos[i] : LT_TH_BSGS, splits ? &splits[i] : nullptr, out[i],
-                         (cudaStream_t)stream, nullptr);
+        cudaStream_t st = (cudaStream_t)stream;
+        // validate everything before queuing anything
+        struct Item {
+            u32 idx;
+            lt_algo algo;
+            lt_split sp;
+        };
+        std::vector<Item> items;
+        for (u32 i = 0; i < count; i++) {
+            const lt_algo algo = algos ? algos[i] : LT_TH_BSGS;
+            items.push_back(Item{i, algo, batch_item_split(ctx, in[i], f[i], algo, splits ? &splits[i] : nullptr,
+                                                           out[i])});
+        }
+        CK(cudaSetDevice(ctx->device));
+        // group the hoisted LTs by (diagonals, level, split); BSGS runs one by one
+        std::vector<bool> done(count, false);
+        for (u32 a = 0; a < count; a++) {
+            if (done[a]) continue;
+            const Item& ia = items[a];
+            if (ia.algo == LT_BSGS) {
+                lt_eval_impl(ctx, in[ia.idx], f[ia.idx], ia.algo, &ia.sp, out[ia.idx], st, nullptr);
+                done[a] = true;
+                continue;
+            }
+            const u32 n1 = ia.sp.n1, n2 = ia.algo == LT_DH_BSGS ? 1 : ia.sp.n2, n3 = ia.algo == LT_DH_BSGS ? ia.sp.n2 : ia.sp.n3;
+            std::vector<LtIO> group;
+            for (u32 b = a; b < count && group.size() < (size_t)DM_MAX_B; b++) {
+                if (done[b]) continue;
+                const Item& ib = items[b];
+                if (ib.algo == LT_BSGS || f[ib.idx] != f[ia.idx] || in[ib.idx]->level != in[ia.idx]->level) continue;
+                const u32 m1 = ib.sp.n1, m2 = ib.algo == LT_DH_BSGS ? 1 : ib.sp.n2,
+                          m3 = ib.algo == LT_DH_BSGS ? ib.sp.n2 : ib.sp.n3;
+                if (m1 != n1 || m2 != n2 || m3 != n3) continue;
+                const u32 level = in[ib.idx]->level;
+                const size_t lw = (size_t)level * ctx->N;
+                group.push_back(LtIO{in[ib.idx]->d, in[ib.idx]->d + lw, out[ib.idx]->d,
+                                     out[ib.idx]->d + (size_t)(level - 1) * ctx->N});
+                done[b] = true;
+            }
+            sched_th_batch(ctx, in[ia.idx]->level, group, f[ia.idx], n1, n2, n3, st);
+        }
+        CK(cudaGetLastError());
     });
 }
 

@@ -92,12 +92,35 @@ struct KsMultiArgs {
 };
 void launch_ks_multi(const KsMultiArgs& a, cudaStream_t st);
 
+// Many independent K4 products (overwrite form, x0 lifted from a Q
+// polynomial) in one launch: entry e reads digits, key and x0 and writes
+// out0/out1.  Entries that share a key are adjacent in the grid.
+constexpr int KS_MAX_BATCH = 128;
+struct KsBatchEntry {
+    const u64* digits;
+    const u64* key;
+    const u64* x0;
+    u64* out0;
+    u64* out1;
+    u32 gal;
+    u32 pad;
+};
+struct KsBatchArgs {
+    KsBatchEntry e[KS_MAX_BATCH];
+    const ModC* mods;
+    const u64* lift_c;
+    const u64* lift_sh;
+    u32 count, level, ext, L, beta, log_n;
+};
+void launch_ks_batch(const KsBatchArgs& a, cudaStream_t st);
+
 // Multi-output plaintext-diagonal multiply-accumulate with the middle
 // (hoisted) key-switch layer fused in (K6).  See ks.cu.
 constexpr int DM_MAX_N1 = 64;
 constexpr int DM_MAX_N2 = 1024;
 constexpr int DM_MAX_K3 = 8;   // giant indices per thread (grid.z covers the rest)
 constexpr int DM_MAX_N3 = 64;
+constexpr int DM_MAX_B = 16;   // ciphertexts per batched launch
 struct DiagMacArgs {
     const ModC* mods;
     const u64* lift_c;
@@ -114,6 +137,15 @@ struct DiagMacArgs {
     u32 level, ext, L, k_p, beta, log_n;
     u32 n1, n2, n3, lift0, diag_level;
     u32* err;                        // set to nonzero when a bounded device wait gives up
+    // Batch of ciphertexts sharing the diagonals and keys: ciphertext b uses
+    // c0[b], c1[b] as its lifted inputs and A[i] + b*bs_ab, B[i] + b*bs_ab,
+    // Dg[i] + b*bs_dg, U0/U1[k] + b*bs_u for the rest.  CTAs of the same
+    // (limb, run) for different b are adjacent in the grid, so the diagonal
+    // and key words they share are read from HBM once.
+    u32 batch;
+    u64 bs_ab, bs_dg, bs_u;
+    const u64* c0[DM_MAX_B];
+    const u64* c1[DM_MAX_B];
 };
 void launch_diag_mac(const DiagMacArgs& a, cudaStream_t st);
 void launch_wait_selftest(u32* err, u64 limit_ns, cudaStream_t st);

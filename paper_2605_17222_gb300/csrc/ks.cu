@@ -83,6 +83,31 @@ __global__ void __launch_bounds__(THREADS) k_ks_multi(const __grid_constant__ Ks
     a.out1[o] = reduce128(acc1, m);
 }
 
+// ------------------------------------------------------------------ K4, many independent products
+__global__ void __launch_bounds__(THREADS) k_ks_batch(const __grid_constant__ KsBatchArgs a) {
+    const u32 N = 1u << a.log_n;
+    const KsBatchEntry& E = a.e[blockIdx.x % a.count];
+    const u32 s = (blockIdx.x / a.count) * THREADS + threadIdx.x;
+    const u32 t = blockIdx.y;
+    if (s >= N) return;
+    const u32 kp = a.ext - a.level;
+    const u32 gmod = t < a.level ? t : a.L + (t - a.level);
+    const ModC m = a.mods[gmod];
+    const u32 src = E.gal ? auto_src(s, E.gal, a.log_n) : s;
+    const size_t key_b = 2ull * (a.L + kp) * N;
+    U128 acc0{0, 0}, acc1{0, 0};
+    for (u32 b = 0; b < a.beta; b++) {
+        const u64 d = E.digits[((size_t)b * a.ext + t) * N + src];
+        const u64* kb = E.key + b * key_b + (size_t)gmod * N + s;
+        mac128(acc0, d, kb[0]);
+        mac128(acc1, d, kb[(size_t)(a.L + kp) * N]);
+    }
+    if (t < a.level) add128(acc0, mul_shoup(E.x0[(size_t)t * N + src], a.lift_c[gmod], a.lift_sh[gmod], m.q));
+    const size_t o = (size_t)t * N + s;
+    E.out0[o] = reduce128(acc0, m);
+    E.out1[o] = reduce128(acc1, m);
+}
+
 // ------------------------------------------------------------------ K6
 // For one word s of limb t and K3 giant indices k (a chunk of the n3 outer
 // rotations) this computes
@@ -102,7 +127,11 @@ __global__ void __launch_bounds__(THREADS, 2) k_diag_mac(const __grid_constant__
     // parked in thread-private shared-memory slots (no barrier needed)
     __shared__ u64 skey[2 * MAXB * THREADS];
     const u32 N = 1u << a.log_n;
-    const u32 s = blockIdx.x * THREADS + threadIdx.x;
+    const u32 bidx = blockIdx.x % a.batch;
+    const u32 s = (blockIdx.x / a.batch) * THREADS + threadIdx.x;
+    const size_t oab = bidx * a.bs_ab, odg = bidx * a.bs_dg, ou = bidx * a.bs_u;
+    const u64* A0 = a.lift0 ? a.c0[bidx] : a.A[0];
+    const u64* B0 = a.lift0 ? a.c1[bidx] : a.B[0];
     const u32 t = blockIdx.y;
     if (s >= N) return;
     const u32 k_first = blockIdx.z * K3;
@@ -156,15 +185,15 @@ __global__ void __launch_bounds__(THREADS, 2) k_diag_mac(const __grid_constant__
             u64 av, bv;
             if (j == 0) {
                 if (lifted) {
-                    av = lift_limb ? mul_shoup(a.A[0][tN + s], lc, lsh, m.q) : 0;
-                    bv = lift_limb ? mul_shoup(a.B[0][tN + s], lc, lsh, m.q) : 0;
+                    av = lift_limb ? mul_shoup(A0[tN + s], lc, lsh, m.q) : 0;
+                    bv = lift_limb ? mul_shoup(B0[tN + s], lc, lsh, m.q) : 0;
                 } else {
-                    av = a.A[i][tN + s];
-                    bv = a.B[i][tN + s];
+                    av = (i ? a.A[i] + oab : A0)[tN + s];
+                    bv = (i ? a.B[i] + oab : B0)[tN + s];
                 }
             } else {
-                const u64* D = a.Dg[i] + tN + src;
-                const u64 xa = (!lifted || lift_limb) ? a.A[i][tN + src] : 0;
+                const u64* D = a.Dg[i] + odg + tN + src;
+                const u64 xa = (!lifted || lift_limb) ? (i ? a.A[i] + oab : A0)[tN + src] : 0;
                 U128 x0{0, 0}, x1{0, 0};
                 if (small_beta) {
                     u64 d[MAXB];
@@ -208,8 +237,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_diag_mac(const __grid_constant__
 #pragma unroll
     for (int kk = 0; kk < K3; kk++) {
         if (kk < (int)k_count) {
-            a.U0[k_first + kk][tN + s] = reduce128(acc0[kk], m);
-            a.U1[k_first + kk][tN + s] = reduce128(acc1[kk], m);
+            a.U0[k_first + kk][ou + tN + s] = reduce128(acc0[kk], m);
+            a.U1[k_first + kk][ou + tN + s] = reduce128(acc1[kk], m);
         }
     }
 }
@@ -279,8 +308,12 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
     __shared__ __align__(8) u64 full_bar[NS];
     const u32 N = 1u << a.log_n;
     const u32 l = threadIdx.x;
-    const u32 run = blockIdx.x;
+    const u32 bidx = blockIdx.x % a.batch;
+    const u32 run = blockIdx.x / a.batch;
     const u32 s = run * RUN + l;
+    const size_t oab = bidx * a.bs_ab, odg = bidx * a.bs_dg, ou = bidx * a.bs_u;
+    const u64* A0 = a.lift0 ? a.c0[bidx] : a.A[0];
+    const u64* B0 = a.lift0 ? a.c1[bidx] : a.B[0];
     const u32 t = blockIdx.y;
     const u32 k_first = blockIdx.z * K3;
     const u32 k_count = min((u32)K3, a.n3 - k_first);
@@ -336,9 +369,11 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
                             a.diags + (size_t)(n1n2 * (k_first + kk)) * dstride + didx + (size_t)hrun[kk] * RUN, RB,
                             bar);
         for (u32 b = 0; b < n_dig; b++)
-            tma_load_1d(st + (size_t)(K3 + b) * RUN, a.Dg[i] + b * dig_b + tN + (size_t)srun * RUN, RB, bar);
-        if (n_ab >= 1) tma_load_1d(st + (size_t)(K3 + beta) * RUN, a.A[i] + tN + (size_t)srun * RUN, RB, bar);
-        if (n_ab == 2) tma_load_1d(st + (size_t)(K3 + beta + 1) * RUN, a.B[i] + tN + (size_t)srun * RUN, RB, bar);
+            tma_load_1d(st + (size_t)(K3 + b) * RUN, a.Dg[i] + odg + b * dig_b + tN + (size_t)srun * RUN, RB, bar);
+        const u64* Ai = i ? a.A[i] + oab : A0;
+        const u64* Bi = i ? a.B[i] + oab : B0;
+        if (n_ab >= 1) tma_load_1d(st + (size_t)(K3 + beta) * RUN, Ai + tN + (size_t)srun * RUN, RB, bar);
+        if (n_ab == 2) tma_load_1d(st + (size_t)(K3 + beta + 1) * RUN, Bi + tN + (size_t)srun * RUN, RB, bar);
     };
 
     if (l == 0) {
@@ -442,8 +477,8 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
 #pragma unroll
     for (int kk = 0; kk < K3; kk++) {
         if (kk < (int)k_count) {
-            a.U0[k_first + kk][tN + s] = reduce128(acc0[kk], m);
-            a.U1[k_first + kk][tN + s] = reduce128(acc1[kk], m);
+            a.U0[k_first + kk][ou + tN + s] = reduce128(acc0[kk], m);
+            a.U1[k_first + kk][ou + tN + s] = reduce128(acc1[kk], m);
         }
     }
 }
@@ -476,7 +511,7 @@ bool try_staged(const DiagMacArgs& a, cudaStream_t st) {
         attr_ok = cudaFuncSetAttribute(k_diag_mac_staged<K3, RUN, NS, KB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DM_SMEM_MAX) == cudaSuccess;
     if (!attr_ok) return false;
-    const dim3 grid(N / RUN, a.ext, (a.n3 + K3 - 1) / K3);
+    const dim3 grid((N / RUN) * a.batch, a.ext, (a.n3 + K3 - 1) / K3);
     k_diag_mac_staged<K3, RUN, NS, KB><<<grid, RUN, sm, st>>>(a);
     return true;
 }
@@ -490,6 +525,13 @@ bool launch_staged(const DiagMacArgs& a, cudaStream_t st) {
 
 void launch_wait_selftest(u32* err, u64 limit_ns, cudaStream_t st) {
     k_wait_selftest<<<1, 32, 0, st>>>(err, limit_ns);
+    count_launch();
+}
+
+void launch_ks_batch(const KsBatchArgs& a, cudaStream_t st) {
+    const u32 N = 1u << a.log_n;
+    ProfScope ps(K_KS_INNER, st);
+    k_ks_batch<<<dim3(((N + THREADS - 1) / THREADS) * a.count, a.ext), THREADS, 0, st>>>(a);
     count_launch();
 }
 
@@ -511,7 +553,7 @@ void launch_diag_mac(const DiagMacArgs& a, cudaStream_t st) {
     const u32 N = 1u << a.log_n;
     u32 k3 = 1;
     while (k3 < a.n3 && k3 < (u32)DM_MAX_K3) k3 *= 2;
-    const dim3 grid((N + THREADS - 1) / THREADS, a.ext, (a.n3 + k3 - 1) / k3);
+    const dim3 grid(((N + THREADS - 1) / THREADS) * a.batch, a.ext, (a.n3 + k3 - 1) / k3);
     ProfScope ps(K_DIAG_MAC, st);
     bool done = false;
     switch (k3) {

@@ -1,0 +1,65 @@
+"""lt_eval_batch: ciphertexts at mixed levels and with mixed algorithms in one
+call give, each, the residues a separate lt_eval gives (and the oracle's),
+bit for bit."""
+import numpy as np
+import pytest
+
+from oracle import lt as olt
+from oracle.workload import add_keys, make_problem
+from paper_2605_17222_gb300 import synth
+
+from gpu_common import TOY_SPLITS, assert_same, ensure_keys, gpu_context, upload_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _encrypt_many(pb, levels, seed):
+    cts, zs = [], []
+    for n, lvl in enumerate(levels):
+        z = synth.slots(seed + n, f"batch/{n}", pb.ctx.N // 2)
+        cts.append(pb.ctx.encrypt(z, pb.s, lvl, pb.scale, seed + n, stream=f"batch/{n}"))
+        zs.append(z)
+    return cts, zs
+
+
+def test_toy_batch_mixed_levels_and_algorithms():
+    pb = make_problem("toy", 0, 64)
+    for algo, split in TOY_SPLITS.items():
+        ensure_keys(pb, algo, split)
+    g = gpu_context("toy")
+    f = upload_problem(g, pb)
+    levels = [4, 3, 2, 4, 3, 4, 4, 2]
+    algos = ["th", "th", "th", "dh", "th", "diag", "bsgs", "th"]
+    cts, zs = _encrypt_many(pb, levels, 50)
+    ins = [g.ct_from_host(np.stack(ct)) for ct in cts]
+    splits = [TOY_SPLITS[a] or (1, 64, 1) for a in algos]
+    outs = g.lt_eval_batch(ins, [f] * len(ins), algos=algos, splits=splits)
+    for n, (ct, lvl, algo) in enumerate(zip(cts, levels, algos)):
+        single, _ = g.lt_eval(ins[n], f, algo, splits[n])
+        got = outs[n].numpy()
+        assert_same(got, single.numpy(), f"batch item {n} ({algo}, level {lvl}) vs single")
+        if n < 3:
+            want = np.stack(olt.run(pb.ctx, algo, ct, pb.diags, pb.keys, TOY_SPLITS[algo], 1)[0])
+            assert_same(got, want, f"batch item {n} vs oracle")
+            scale = pb.scale * pb.diag_scale / pb.ctx.q[lvl - 1]
+            y = pb.ctx.decrypt((got[0], got[1]), pb.s, scale)
+            assert np.max(np.abs(y - olt.fp64_reference(zs[n], pb.fvals))) < 1e-5
+
+
+def test_full_size_batch_matches_single():
+    """N = 2^16: five ciphertexts at levels 24 and 16 sharing 256 diagonals, TH (4,8,8)."""
+    pb = make_problem("n16", 7, 256)
+    split = (4, 8, 8)
+    add_keys(pb, olt.rotation_set("th", 256, split, 1, pb.ctx.N // 2))
+    g = gpu_context("n16")
+    f = upload_problem(g, pb)
+    levels = [24, 16, 24, 16, 24]
+    cts, zs = _encrypt_many(pb, levels, 70)
+    ins = [g.ct_from_host(np.stack(ct)) for ct in cts]
+    outs = g.lt_eval_batch(ins, [f] * len(ins), algos=["th"] * len(ins), splits=[split] * len(ins))
+    for n in range(len(ins)):
+        single, _ = g.lt_eval(ins[n], f, "th", split)
+        assert_same(outs[n].numpy(), single.numpy(), f"item {n} level {levels[n]}")
+    # one item against the oracle at the lower level
+    want = np.stack(olt.lt_th_bsgs(pb.ctx, cts[1], pb.diags, pb.keys, *split)[0])
+    assert_same(outs[1].numpy(), want, "level-16 item vs oracle")
