@@ -56,6 +56,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--diags", type=int, default=256, help="number of diagonals (256 = the benchmark workload)")
     ap.add_argument("--level", type=int, default=24, help="ciphertext level (24 = the benchmark workload)")
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+                    help="single: one LT per step (the headline); batched: 64 ciphertexts at levels "
+                         "{8,16,24} and one shared 256-diagonal matrix per step; serving: Poisson "
+                         "arrivals of LT requests through the continuous-batching server")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     return ap.parse_args()
 
 
@@ -415,6 +421,187 @@ def run_ours(args, dist: Dist):
     return result
 
 
+def run_batched(args, dist: Dist):
+    """64 ciphertexts at N=2^16 with levels drawn from {8, 16, 24} (seed 2), all
+    multiplied by one shared 256-diagonal matrix: one recorded lt_eval_batch per
+    step, against the same 64 LTs as sequential lt_eval calls."""
+    import numpy as np
+    import torch
+    from paper_2605_17222_gb300 import binding, synth
+    device = f"cuda:{dist.local}"
+    torch.cuda.set_device(dist.local)
+    ps = synth.param_set(PARAMS)
+    g = binding.Context.from_params(ps, device=dist.local)
+    n_ct = 64
+    levels = [int(v) for v in np.random.default_rng(2).choice([8, 16, 24], n_ct)]
+    splits = {lv: g.choose_split("th", lv, D) for lv in sorted(set(levels))}
+    rots = sorted({r for lv, sp in splits.items() for r in g.required_rotations("th", sp, D, 1)})
+    for r in rots:
+        t = synth.uniform_mod_device(SEED, f"key/{r}", ps.moduli, ps.n, count=2 * g.beta_max, device=device)
+        g.upload_rotation_key_device(r, t)
+        del t
+    top = list(ps.q) + list(ps.p)
+    dt = synth.uniform_mod_device(SEED, "diag", top, ps.n, count=D, device=device)
+    f = g.upload_diagonals_device(dt, stride=1, level=ps.L)
+    del dt
+    cts = [g.ct_wrap(synth.uniform_mod_device(SEED + 1 + n, f"ct/{n}", list(ps.q[:lv]), ps.n, count=2,
+                                              device=device), lv) for n, lv in enumerate(levels)]
+    outs = [g.ct_empty(lv - 1) for lv in levels]
+    sp_list = [splits[lv] for lv in levels]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dist.barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        return dist.max(e0.elapsed_time(e1))
+
+    def sequential():
+        for c, o, sp in zip(cts, outs, sp_list):
+            g.lt_eval(c, f, "th", sp, out=o)
+
+    rec = g.lt_graph(cts, [f] * n_ct, algos=["th"] * n_ct, splits=sp_list, outs=outs)
+    steps = max(1, args.steps)
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    ms_graph = timed(lambda: rec.launch(), steps)
+    ms_batch = timed(lambda: g.lt_eval_batch(cts, [f] * n_ct, algos=["th"] * n_ct, splits=sp_list, outs=outs),
+                     steps)
+    ms_seq = timed(sequential, steps)
+    clk = clocks.stop()
+    rec.close()
+    # compulsory bytes of one step: diagonals and keys once per level used, every ciphertext in and out
+    limb = 8 * ps.n
+    comp = 0
+    for lv, sp in splits.items():
+        beta = g.beta(lv)
+        ext = lv + ps.k
+        keys = (sp[0] - 1) + (sp[1] - 1) + (sp[2] - 1)
+        comp += limb * (D * ext + keys * 2 * beta * ext)
+    comp += sum(limb * (2 * lv + 2 * (lv - 1)) for lv in levels)
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    val = dist.world * n_ct * steps / (ms_graph / 1e3)
+    return {
+        "metric": METRIC, "value": round(val, 3), "unit": "LT/s", "n_gpus": dist.world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_graph / steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (uniform residues drawn on the device; seeded)",
+        "config": {"workload": f"batched: {n_ct} ciphertexts, N=2^16, levels from {{8,16,24}} (seed 2), one shared "
+                               f"{D}-diagonal matrix; one recorded lt_eval_batch per step",
+                   "levels": {str(lv): levels.count(lv) for lv in sorted(set(levels))},
+                   "splits": {str(lv): list(sp) for lv, sp in splits.items()},
+                   "l2": "inputs larger than L2; no flush"},
+        "batched_graph_lt_per_s": round(val, 3),
+        "batched_call_lt_per_s": round(dist.world * n_ct * steps / (ms_batch / 1e3), 3),
+        "sequential_lt_per_s": round(dist.world * n_ct * steps / (ms_seq / 1e3), 3),
+        "speedup_vs_sequential": round(ms_seq / ms_graph, 3),
+        "hbm_roofline_batch": {"compulsory_bytes": comp,
+                               "frac": round(comp / (ms_graph / steps / 1e3) / 1e9 / peak, 4)},
+        "clocks": clk,
+    }
+
+
+def run_serving(args, dist: Dist):
+    """Poisson arrivals (rate, duration; seed 4) of single-LT requests, each with
+    N from {2^15, 2^16}, 32..512 diagonals (powers of two) and a level of
+    6..24 (6..16 at N = 2^15); keys and matrices resident; admission under a
+    150 GB HBM budget; continuous batching over 4 streams."""
+    import numpy as np
+    import torch
+    from paper_2605_17222_gb300 import binding, synth
+    from paper_2605_17222_gb300.serving import LtServer, Request, percentile, run_open_loop
+    device = f"cuda:{dist.local}"
+    torch.cuda.set_device(dist.local)
+    rng = np.random.default_rng(4 + dist.rank)
+    sizes = [32, 64, 128, 256, 512]
+    sets = {16: synth.param_set("n16"), 15: synth.param_set("n15")}
+    lv_range = {16: (6, 24), 15: (6, 16)}
+    ctxs, mats, pools, resident = {}, {}, {}, 0
+    for ln, ps in sets.items():
+        g = binding.Context.from_params(ps, device=dist.local)
+        ctxs[ln] = g
+        lo, hi = lv_range[ln]
+        rots = set()
+        for d in sizes:
+            for lv in range(lo, hi + 1):
+                rots |= set(g.required_rotations("th", g.choose_split("th", lv, d), d, 1))
+        for r in sorted(rots):
+            t = synth.uniform_mod_device(SEED, f"key/{ln}/{r}", ps.moduli, ps.n, count=2 * g.beta_max, device=device)
+            g.upload_rotation_key_device(r, t)
+            resident += t.numel() * 8
+            del t
+        top = list(ps.q) + list(ps.p)
+        for d in sizes:
+            t = synth.uniform_mod_device(SEED, f"diag/{ln}/{d}", top, ps.n, count=d, device=device)
+            mats[(ln, d)] = g.upload_diagonals_device(t, stride=1, level=ps.L)
+            resident += t.numel() * 8
+            del t
+        for lv in range(lo, hi + 1):
+            pools[(ln, lv)] = [g.ct_wrap(synth.uniform_mod_device(SEED + c, f"ct/{ln}/{lv}/{c}", list(ps.q[:lv]),
+                                                                  ps.n, count=2, device=device), lv)
+                               for c in range(2)]
+    torch.cuda.synchronize()
+    n_req = int(args.rate * args.duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, n_req)).tolist()
+    specs = []
+    for i in range(n_req):
+        ln = int(rng.choice([15, 16]))
+        lo, hi = lv_range[ln]
+        specs.append((ln, int(rng.choice(sizes)), int(rng.integers(lo, hi + 1))))
+
+    def make_request(i, t_arr):
+        ln, d, lv = specs[i]
+        return Request(i, ln, mats[(ln, d)], pools[(ln, lv)][i % 2], t_arr)
+
+    srv = LtServer(ctxs, hbm_budget=150e9, resident_bytes=resident, streams=4, max_batch=16)
+    # warm-up: one request of every (context, level, matrix) shape sets up tables and kernel attributes
+    for ln in sets:
+        lo, hi = lv_range[ln]
+        for lv in range(lo, hi + 1):
+            for d in sizes:
+                srv.submit(Request(-1, ln, mats[(ln, d)], pools[(ln, lv)][0], time.perf_counter()))
+    srv.drain(timeout_s=600)
+    srv.stats = type(srv.stats)()
+    srv.completed = []
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run_open_loop(srv, arrivals, make_request)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    dist.barrier()
+    clk = clocks.stop()
+    lat = srv.stats.latencies
+    done = dist.world * srv.stats.completed
+    wall_max = dist.max(wall)
+    return {
+        "metric": METRIC, "value": round(done / wall_max, 3), "unit": "LT/s", "n_gpus": dist.world,
+        "steps": srv.stats.completed, "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (uniform residues drawn on the device; seeded)",
+        "config": {"workload": f"serving: Poisson arrivals {args.rate:g} req/s for {args.duration:g} s (seed 4), "
+                               f"N in {{2^15, 2^16}}, {sizes[0]}..{sizes[-1]} diagonals, levels 6..24 (6..16 at "
+                               f"2^15), keys and matrices resident, 150 GB admission budget, 4 streams",
+                   "resident_bytes": resident},
+        "p50_ms": round(1e3 * percentile(lat, 50), 3), "p99_ms": round(1e3 * percentile(lat, 99), 3),
+        "mean_ms": round(1e3 * float(np.mean(lat)), 3) if lat else None,
+        "offered_rate": args.rate, "completed": srv.stats.completed, "wall_s": round(wall_max, 3),
+        "batches": srv.stats.batches, "mean_batch": round(srv.stats.completed / max(1, srv.stats.batches), 2),
+        "admission_waits": srv.stats.admission_waits, "max_inflight_scratch_bytes": srv.stats.max_inflight_bytes,
+        "clocks": clk,
+    }
+
+
 def run_reference(args, dist: Dist):
     """The CPU oracle as the reference arm, on this host's cores."""
     global D, LEVEL
@@ -461,6 +648,10 @@ def main():
     try:
         if args.impl == "reference":
             res = run_reference(args, dist)
+        elif args.workload == "batched":
+            res = run_batched(args, dist)
+        elif args.workload == "serving":
+            res = run_serving(args, dist)
         else:
             res = run_ours(args, dist)
         if dist.rank == 0 and res is not None:

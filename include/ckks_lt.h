@@ -159,6 +159,19 @@ ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* i
                           const ckks_diags* const* f, const lt_algo* algos, const lt_split* splits,
                           ckks_ct* const* out, void* stream);
 
+/* A recorded batch.  lt_graph_create runs lt_eval_batch once with these
+ * arguments (which also sets up every table the batch needs), then records
+ * the same work into a CUDA graph; lt_graph_launch replays it on `stream`,
+ * recomputing every output from the current contents of the inputs, with no
+ * host-side work.  The ciphertexts, diagonals and keys named at creation must
+ * stay alive and keep their buffers while the graph exists; the graph owns
+ * its scratch memory.  Replays of one graph must not overlap in time. */
+typedef struct lt_graph lt_graph;
+ckks_status lt_graph_create(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* in, const ckks_diags* const* f,
+                            const lt_algo* algos, const lt_split* splits, ckks_ct* const* out, lt_graph** graph);
+ckks_status lt_graph_launch(lt_graph* graph, void* stream);
+ckks_status lt_graph_destroy(lt_graph* graph);
+
 /* Rotation amounts (mod N/2, ascending, multiples of stride) whose keys the
  * algorithm needs for n_diag diagonals and this split; returns how many were
  * written (at most cap), or -1 on a bad split. */

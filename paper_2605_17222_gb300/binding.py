@@ -81,6 +81,9 @@ def lib():
         "ckks_rescale": [P, U32, P, P, P],
         "ckks_automorphism": [P, U32, P, I32, P, P],
         "ckks_device_status": [P],
+        "lt_graph_create": [P, U32, P, P, P, P, P, PP],
+        "lt_graph_launch": [P, P],
+        "lt_graph_destroy": [P],
         "ckks_selftest_bounded_wait": [P, U32, P],
     }
     for name, args in sig.items():
@@ -180,6 +183,22 @@ class Diagonals:
         if self.handle:
             check(lib().ckks_free_diags(self.handle))
             self.handle = None
+
+
+class RecordedBatch:
+    """A replayable lt_eval_batch (lt_graph_*)."""
+
+    def __init__(self, handle, outs, keep):
+        self.h, self.outs, self._keep = handle, outs, keep
+
+    def launch(self, stream=None):
+        check(lib().lt_graph_launch(self.h, _stream(stream)))
+        return self.outs
+
+    def close(self):
+        if self.h:
+            check(lib().lt_graph_destroy(self.h))
+            self.h = None
 
 
 class Context:
@@ -316,6 +335,17 @@ class Context:
             sp = (Split * n)(*[Split(*(tuple(s) + (1,) * (3 - len(s)))) for s in splits])
         check(lib().lt_eval_batch(self.h, n, arr(cts), arr(diags), al, sp, arr(outs), _stream(stream)))
         return outs
+
+    def lt_graph(self, cts, diags, algos=None, splits=None, outs=None):
+        """Record one lt_eval_batch into a replayable graph (see lt_graph_create)."""
+        n = len(cts)
+        outs = outs or [self.ct_empty(c.level - 1) for c in cts]
+        arr = lambda xs: (ctypes.c_void_p * n)(*[x.handle for x in xs])
+        al = (ctypes.c_int * n)(*[ALGOS[a] for a in algos]) if algos else None
+        sp = (Split * n)(*[Split(*(tuple(s) + (1,) * (3 - len(s)))) for s in splits]) if splits else None
+        h = ctypes.c_void_p()
+        check(lib().lt_graph_create(self.h, n, arr(cts), arr(diags), al, sp, arr(outs), ctypes.byref(h)))
+        return RecordedBatch(h, outs, (cts, diags))
 
     # ----------------------------------------------------------- steps (device tensors)
     def ntt(self, poly, level: int, ext: bool, inverse: bool, stream=None):

@@ -1264,6 +1264,77 @@ ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* i
     });
 }
 
+// ------------------------------------------------------------------ recorded batches
+}  // extern "C"
+
+struct lt_graph {
+    ckks_ctx* ctx;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" {
+
+ckks_status lt_graph_create(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* in, const ckks_diags* const* f,
+                            const lt_algo* algos, const lt_split* splits, ckks_ct* const* out, lt_graph** graph) {
+    cudaStream_t st = nullptr;
+    lt_graph* gr = nullptr;
+    ckks_status rc = guarded([&] {
+        if (!ctx || !graph) fail(CKKS_EINVAL, "null argument");
+        *graph = nullptr;
+        CK(cudaSetDevice(ctx->device));
+        CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    });
+    if (rc != CKKS_OK) return rc;
+    // one plain run: validates the batch and sets up every table and kernel attribute it needs
+    rc = lt_eval_batch(ctx, count, in, f, algos, splits, out, st);
+    if (rc == CKKS_OK)
+        rc = guarded([&] {
+            CK(cudaStreamSynchronize(st));
+            gr = new lt_graph{ctx};
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        });
+    if (rc == CKKS_OK) {
+        const ckks_status run = lt_eval_batch(ctx, count, in, f, algos, splits, out, st);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        rc = run != CKKS_OK ? run : guarded([&] {
+            CK(e);
+            gr->graph = g;
+            CK(cudaGraphInstantiate(&gr->exec, g, 0));
+            *graph = gr;
+            gr = nullptr;
+        });
+        if (rc != CKKS_OK && g && gr && !gr->graph) cudaGraphDestroy(g);
+    }
+    if (gr) {
+        if (gr->exec) cudaGraphExecDestroy(gr->exec);
+        if (gr->graph) cudaGraphDestroy(gr->graph);
+        delete gr;
+    }
+    if (st) cudaStreamDestroy(st);
+    return rc;
+}
+
+ckks_status lt_graph_launch(lt_graph* graph, void* stream) {
+    return guarded([&] {
+        if (!graph) fail(CKKS_EINVAL, "null argument");
+        CK(cudaSetDevice(graph->ctx->device));
+        CK(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+        count_launch();
+    });
+}
+
+ckks_status lt_graph_destroy(lt_graph* graph) {
+    return guarded([&] {
+        if (!graph) return;
+        cudaSetDevice(graph->ctx->device);
+        if (graph->exec) cudaGraphExecDestroy(graph->exec);
+        if (graph->graph) cudaGraphDestroy(graph->graph);
+        delete graph;
+    });
+}
+
 // ------------------------------------------------------------------ steps
 ckks_status ckks_poly_ntt(ckks_ctx* ctx, uint64_t* poly, uint32_t level, int ext, int inverse, void* stream) {
     return guarded([&] {
