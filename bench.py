@@ -255,11 +255,11 @@ def cores_used() -> int:
 
 
 # ----------------------------------------------------------------------------- main arms
-def make_inputs(g, ps, split, algo, device):
+def make_inputs(g, ps, splits, algo, device):
     import torch
     from paper_2605_17222_gb300 import synth
     N = ps.n
-    rots = g.required_rotations(algo, split if algo != "diag" else None, D, 1)
+    rots = sorted({r for sp in splits for r in g.required_rotations(algo, sp if algo != "diag" else None, D, 1)})
     keys_t = {}
     for r in rots:
         t = synth.uniform_mod_device(SEED, f"key/{r}", ps.moduli, N, count=2 * g.beta_max, device=device)
@@ -284,13 +284,21 @@ def run_ours(args, dist: Dist):
     ps = synth.param_set(PARAMS)
     g = binding.Context.from_params(ps, device=dist.local)
     algo = args.algo
+    tuned_ms = None
     if args.split:
         split = tuple(int(x) for x in args.split.split(","))
+        split3 = tuple(split) + (1,) * (3 - len(split))
+        rots, keys_t, diags_t, f, ct_t = make_inputs(g, ps, [split3], algo, device)
+        ct = g.ct_wrap(ct_t, LEVEL)
     else:
-        split = g.choose_split(algo, LEVEL, D)
-    split3 = tuple(split) + (1,) * (3 - len(split))
-    rots, keys_t, diags_t, f, ct_t = make_inputs(g, ps, split3, algo, device)
-    ct = g.ct_wrap(ct_t, LEVEL)
+        # the library's autotuner: keys for the cost model's best candidates, each timed once here
+        cands = [g.choose_split(algo, LEVEL, D)] if algo == "diag" else g.candidate_splits(algo, LEVEL, D, 6)
+        rots, keys_t, diags_t, f, ct_t = make_inputs(g, ps, cands, algo, device)
+        ct = g.ct_wrap(ct_t, LEVEL)
+        if algo == "diag":
+            split3 = (1, D, 1)
+        else:
+            split3, tuned_ms = g.autotune(algo, ct, f, len(cands))
     out = g.ct_empty(LEVEL - 1)
     keep_host_copy = not args.no_cpu_baseline and dist.rank == 0 and dist.world == 1
     if not keep_host_copy:  # the library holds its own copies
@@ -400,6 +408,8 @@ def run_ours(args, dist: Dist):
         "config": {"workload": f"single LT: N=2^16, level {LEVEL} (Q = 55b + 23x40b), 4x60b special primes, "
                                f"dnum 6, {D} consecutive diagonals, one ciphertext at the top level",
                    "algo": algo, "split": list(split3), "parallelism": f"replicas x{dist.world}",
+                   "split_choice": "given" if args.split else f"autotuned over the cost model's best candidates "
+                                                               f"({tuned_ms:.3f} ms when measured)",
                    "l2": "inputs larger than L2 (keys + diagonals resident, > 6 GB per step); no flush"},
         "hbm_roofline_lt": (None if lt_bytes is None else {
             "compulsory_bytes": lt_bytes, "achieved_gbs": round(lt_bytes / (max_ms / args.steps / 1e3) / 1e9, 1),

@@ -178,7 +178,23 @@ ckks_status lt_graph_destroy(lt_graph* graph);
 int32_t lt_required_rotations(const ckks_ctx* ctx, lt_algo algo, const lt_split* split,
                               uint32_t n_diag, int32_t stride, int32_t* rot_out, uint32_t cap);
 
-/* The split the library would choose for (algo, level, n_diag). */
+/* The cost model's ranking of the admissible splits for (algo, level,
+ * n_diag), fastest first; writes at most cap and returns how many. */
+int32_t lt_candidate_splits(const ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out,
+                            uint32_t cap);
+
+/* Measuring autotuner (split selection per shape): ranks every admissible
+ * split of f's n_diag for `algo` with the library's cost model, keeps the
+ * first max_candidates whose rotation keys are all uploaded, times each on
+ * `sample` (its level and f's stride define the shape), and records the
+ * fastest for that (algo, level, n_diag, stride); lt_eval and lt_eval_batch
+ * then use it whenever no split is given.  Synchronous; allocates one scratch
+ * ciphertext.  ENOKEY if no candidate has all of its keys. */
+ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, const ckks_diags* f,
+                        uint32_t max_candidates, lt_split* chosen, double* best_ms);
+
+/* The split the library would choose for (algo, level, n_diag) with stride 1:
+ * the autotuned one if lt_autotune has measured that shape, else the model's. */
 ckks_status lt_choose_split(ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out);
 
 /* ------------------------------------------------------------------ steps

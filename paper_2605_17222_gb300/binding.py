@@ -73,6 +73,7 @@ def lib():
         "lt_eval": [P, P, P, I, P, P, P, P],
         "lt_eval_batch": [P, U32, P, P, P, P, P, P],
         "lt_choose_split": [P, I, U32, U32, P],
+        "lt_autotune": [P, I, P, P, U32, P, P],
         "ckks_poly_ntt": [P, P, U32, I, I, P],
         "ckks_decompose": [P, U32, P, I32, P, P],
         "ckks_ks_inner": [P, U32, P, I32, I32, P, I, P, P, I, P],
@@ -276,6 +277,25 @@ class Context:
         if n < 0:
             raise CkksError(1, "bad split")
         return list(buf[:n])
+
+    def autotune(self, algo: str, sample: "Ciphertext", diags: "Diagonals", max_candidates: int = 6):
+        """Time the model's best candidate splits on `sample` and keep the fastest."""
+        sp, ms = Split(), ctypes.c_double()
+        check(lib().lt_autotune(self.h, ALGOS[algo], sample.handle, diags.handle, max_candidates, ctypes.byref(sp),
+                                ctypes.byref(ms)))
+        return sp.tuple(), ms.value
+
+    def candidate_splits(self, algo: str, level: int, n_diag: int, count: int):
+        """The cost model's `count` best splits, fastest first (lt_candidate_splits)."""
+        L = lib()
+        L.lt_candidate_splits.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_void_p, ctypes.c_uint32]
+        L.lt_candidate_splits.restype = ctypes.c_int32
+        buf = (Split * count)()
+        n = L.lt_candidate_splits(self.h, ALGOS[algo], level, n_diag, buf, count)
+        if n < 0:
+            raise CkksError(1, "bad arguments")
+        return [buf[i].tuple() for i in range(n)]
 
     def choose_split(self, algo: str, level: int, n_diag: int):
         sp = Split()

@@ -10,6 +10,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ckks_lt.h"
@@ -136,6 +137,7 @@ struct ckks_ctx {
     NttTables T{};
     std::map<u32, LevelConsts> levels;
     std::map<u32, u64*> keys;  // rotation (mod N/2) -> [beta_max][2][L+K][N]
+    std::map<std::tuple<int, u32, u32, int32_t>, lt_split> tuned;  // (algo, level, D, stride) -> measured best
     std::mutex mu;
     size_t bytes = 0;
 
@@ -785,7 +787,8 @@ std::vector<int64_t> rotations(lt_algo algo, const lt_split& sp, u32 D) {
 namespace {
 double model_time(const ckks_ctx* C, lt_algo algo, u32 level, u32 D, const lt_split& sp) {
     const double limb = 8.0 * C->N, ext = level + C->K, beta = (double)((level + C->alpha - 1) / C->alpha);
-    const double bw = 5.5e12, ntt_rate = 9.0e11;  // bytes/s, butterflies/s
+    // rates of this library's kernels on GB300 (fitted to measured LTs at N = 2^16)
+    const double bw = 5.5e12, ntt_rate = 4.3e11, mac_rate = 7.6e11;  // bytes/s, butterflies/s, MAC/s
     const double ntt = (C->N / 2.0) * C->log_n;
     double keys, dec, md, kspairs;
     if (algo == LT_TH_BSGS) {
@@ -814,11 +817,49 @@ double model_time(const ckks_ctx* C, lt_algo algo, u32 level, u32 D, const lt_sp
     bytes += limb * dec * beta * ext * 2.0;
     double flops = dec * (level + beta * (ext - C->alpha)) * ntt + md * (C->K + level) * ntt;
     double mac = (kspairs * 2 * beta * ext + 2.0 * D * ext) * C->N;
-    return bytes / bw + flops / ntt_rate + mac / 2.0e12;
+    return bytes / bw + flops / ntt_rate + mac / mac_rate;
 }
 }  // namespace
 
-static lt_split choose_split(const ckks_ctx* C, lt_algo algo, u32 level, u32 D) {
+// Every admissible split of D for `algo`, fastest first by the model.
+static std::vector<lt_split> ranked_splits(const ckks_ctx* C, lt_algo algo, u32 level, u32 D) {
+    std::vector<std::pair<double, lt_split>> all;
+    if (algo == LT_DIAG) return {lt_split{1, D, 1}};
+    std::vector<u32> divs;
+    for (u32 d = 1; d <= D; d++)
+        if (D % d == 0) divs.push_back(d);
+    for (u32 a : divs)
+        for (u32 b : divs) {
+            if ((u64)a * b > D || D % ((u64)a * b)) continue;
+            lt_split sp;
+            if (algo == LT_TH_BSGS) {
+                sp = lt_split{a, b, D / (a * b)};
+                if (sp.n1 > (u32)DM_MAX_N1 || sp.n3 > (u32)DM_MAX_N3 || sp.n2 > (u32)DM_MAX_N2) continue;
+            } else {
+                if (a * b != D) continue;
+                sp = lt_split{a, b, 1};
+                if (sp.n1 > (u32)DM_MAX_N1 || sp.n2 > (u32)DM_MAX_N3) continue;
+            }
+            all.push_back({model_time(C, algo, level, D, sp), sp});
+        }
+    std::stable_sort(all.begin(), all.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    std::vector<lt_split> out;
+    for (auto& e : all) out.push_back(e.second);
+    return out;
+}
+
+static lt_split choose_split(const ckks_ctx* C, lt_algo algo, u32 level, u32 D, int32_t stride = 1) {
+    if (algo == LT_DIAG) return lt_split{1, D, 1};
+    {
+        std::lock_guard<std::mutex> g(const_cast<ckks_ctx*>(C)->mu);
+        auto it = C->tuned.find(std::make_tuple((int)algo, level, D, stride));
+        if (it != C->tuned.end()) return it->second;
+    }
+    std::vector<lt_split> r = ranked_splits(C, algo, level, D);
+    return r.empty() ? lt_split{0, 0, 0} : r[0];
+}
+
+[[maybe_unused]] static lt_split choose_split_model_only(const ckks_ctx* C, lt_algo algo, u32 level, u32 D) {
     lt_split best{0, 0, 0};
     if (algo == LT_DIAG) return lt_split{1, D, 1};
     double bt = 1e300;
@@ -1157,6 +1198,76 @@ int32_t lt_required_rotations(const ckks_ctx* ctx, lt_algo algo, const lt_split*
     return (int32_t)std::min<u32>(n, cap);
 }
 
+static void lt_eval_impl(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_algo algo, const lt_split* split,
+                         ckks_ct* out, cudaStream_t st, lt_split* chosen);
+
+int32_t lt_candidate_splits(const ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out,
+                            uint32_t cap) {
+    if (!ctx) return -1;
+    const std::vector<lt_split> r = ranked_splits(ctx, algo, level, n_diag);
+    uint32_t n = 0;
+    for (const lt_split& sp : r) {
+        if (n >= cap) break;
+        if (out) out[n] = sp;
+        n++;
+    }
+    return (int32_t)n;
+}
+
+ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, const ckks_diags* f,
+                        uint32_t max_candidates, lt_split* chosen, double* best_ms) {
+    cudaStream_t st = nullptr;
+    ckks_ct* out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ckks_status rc = guarded([&] {
+        if (!ctx || !sample || !f) fail(CKKS_EINVAL, "null argument");
+        const u32 level = sample->level, D = f->n_diag;
+        if (level < 2 || level > f->level) fail(CKKS_EINVAL, "bad sample level");
+        CK(cudaSetDevice(ctx->device));
+        // candidates: the model's ranking, keeping the splits whose keys are all present
+        std::vector<lt_split> cand;
+        for (const lt_split& sp : ranked_splits(ctx, algo, level, D)) {
+            bool ok = true;
+            for (int64_t r : rotations(algo, sp, D))
+                if (!ctx->keys.count(ctx->rotkey(r * f->stride))) ok = false;
+            if (ok) cand.push_back(sp);
+            if (cand.size() >= std::max<u32>(1, max_candidates)) break;
+        }
+        if (cand.empty()) fail(CKKS_ENOKEY, "no candidate split has all of its rotation keys");
+        CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        out = new ckks_ct{ctx, level - 1, ctx->dalloc(2ull * (level - 1) * ctx->N), true};
+        double best = 1e300;
+        lt_split bsp = cand[0];
+        for (const lt_split& sp : cand) {
+            lt_eval_impl(ctx, sample, f, algo, &sp, out, st, nullptr);  // warm-up (tables, attributes)
+            CK(cudaEventRecord(e0, st));
+            const int reps = 3;
+            for (int r = 0; r < reps; r++) lt_eval_impl(ctx, sample, f, algo, &sp, out, st, nullptr);
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms / reps < best) best = ms / reps, bsp = sp;
+        }
+        {
+            std::lock_guard<std::mutex> g(ctx->mu);
+            ctx->tuned[std::make_tuple((int)algo, level, D, f->stride)] = bsp;
+        }
+        if (chosen) *chosen = bsp;
+        if (best_ms) *best_ms = best;
+    });
+    if (out) {
+        ctx->dfree(out->d, 2ull * out->level * ctx->N);
+        delete out;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return rc;
+}
+
 ckks_status lt_choose_split(ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out) {
     return guarded([&] {
         if (!ctx || !out) fail(CKKS_EINVAL, "null argument");
@@ -1175,7 +1286,8 @@ static void lt_eval_impl(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, 
     if (out->level != level - 1) fail(CKKS_EINVAL, "output level must be input level - 1");
     if (out->d == in->d) fail(CKKS_EINVAL, "output must not alias input");
     const u32 D = f->n_diag;
-    lt_split sp = (split && (split->n1 || split->n2 || split->n3)) ? *split : choose_split(ctx, algo, level, D);
+    lt_split sp = (split && (split->n1 || split->n2 || split->n3)) ? *split
+                                                                   : choose_split(ctx, algo, level, D, f->stride);
     if (algo == LT_DIAG) sp = lt_split{1, D, 1};
     if (algo != LT_TH_BSGS && sp.n3 == 0) sp.n3 = 1;
     validate_split(algo, D, sp);
@@ -1207,7 +1319,8 @@ static lt_split batch_item_split(ckks_ctx* ctx, const ckks_ct* in, const ckks_di
     if (level < 2 || level > f->level || out->level != level - 1) fail(CKKS_EINVAL, "bad levels in the batch");
     if (out->d == in->d) fail(CKKS_EINVAL, "output must not alias input");
     const u32 D = f->n_diag;
-    lt_split sp = (split && (split->n1 || split->n2 || split->n3)) ? *split : choose_split(ctx, algo, level, D);
+    lt_split sp = (split && (split->n1 || split->n2 || split->n3)) ? *split
+                                                                   : choose_split(ctx, algo, level, D, f->stride);
     if (algo == LT_DIAG) sp = lt_split{1, D, 1};
     if (algo != LT_TH_BSGS && sp.n3 == 0) sp.n3 = 1;
     validate_split(algo, D, sp);

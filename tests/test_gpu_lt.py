@@ -136,3 +136,20 @@ def test_full_size_autotuned_th(full):
     out, chosen = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, "th")
     assert chosen == split
     assert_same(out.numpy(), oracle_lt(pb, "th", split), f"full auto {split}")
+
+
+def test_toy_measuring_autotuner(toy):
+    """lt_autotune times the model's candidates that have keys, records the
+    fastest, and lt_eval without a split then uses it (bit-exact with the oracle)."""
+    pb, g, f = toy
+    ct = g.ct_from_host(np.stack(pb.ct))
+    cands = g.candidate_splits("th", pb.level, pb.D, 4)
+    assert all(a * b * c == pb.D for a, b, c in cands)
+    for sp in cands:
+        ensure_keys(pb, "th", sp)
+    upload_problem(g, pb)
+    split, ms = g.autotune("th", ct, f, 4)
+    assert split in cands and ms > 0
+    out, chosen = g.lt_eval(ct, f, "th")
+    assert chosen == split
+    assert_same(out.numpy(), oracle_lt(pb, "th", split), f"autotuned {split}")
