@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--diags", type=int, default=256, help="number of diagonals (256 = the benchmark workload)")
     ap.add_argument("--level", type=int, default=24, help="ciphertext level (24 = the benchmark workload)")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "uneven", "serving"],
                     help="single: one LT per step (the headline); batched: 64 ciphertexts at levels "
                          "{8,16,24} and one shared 256-diagonal matrix per step; serving: Poisson "
                          "arrivals of LT requests through the continuous-batching server")
@@ -520,6 +520,93 @@ def run_batched(args, dist: Dist):
     }
 
 
+def run_uneven(args, dist: Dist):
+    """128 LTs per step at N = 2^16: diagonal counts from {16, 64, 256, 1024},
+    offsets consecutive or strided by 2^k (k = 1..4, D 2^k <= N/2), levels
+    uniform in 6..24 (seed 3); one matrix per distinct (D, stride) shape shared
+    by the LTs of that shape; one split per shape from the cost model; one
+    recorded lt_eval_batch per step against 128 sequential lt_eval calls."""
+    import numpy as np
+    import torch
+    from paper_2605_17222_gb300 import binding, synth
+    device = f"cuda:{dist.local}"
+    torch.cuda.set_device(dist.local)
+    ps = synth.param_set(PARAMS)
+    g = binding.Context.from_params(ps, device=dist.local)
+    rng = np.random.default_rng(3)
+    n_lt = 128
+    items = []
+    for _ in range(n_lt):
+        d = int(rng.choice([16, 64, 256, 1024]))
+        ks = [k for k in range(1, 5) if d * (1 << k) <= ps.n // 2]
+        stride = 1 if rng.random() < 0.5 or not ks else 1 << int(rng.choice(ks))
+        items.append((d, stride, int(rng.integers(6, 25))))
+    shapes = sorted({(d, st) for d, st, _ in items})
+    split_of = {sh: g.choose_split("th", ps.L, sh[0]) for sh in shapes}
+    rots = sorted({(r * 1) % (ps.n // 2) for (d, st) in shapes
+                   for r in g.required_rotations("th", split_of[(d, st)], d, st)})
+    for r in rots:
+        t = synth.uniform_mod_device(SEED, f"key/{r}", ps.moduli, ps.n, count=2 * g.beta_max, device=device)
+        g.upload_rotation_key_device(r, t)
+        del t
+    top = list(ps.q) + list(ps.p)
+    mats = {}
+    for (d, st) in shapes:
+        t = synth.uniform_mod_device(SEED, f"diag/{d}/{st}", top, ps.n, count=d, device=device)
+        mats[(d, st)] = g.upload_diagonals_device(t, stride=st, level=ps.L)
+        del t
+    torch.cuda.empty_cache()
+    cts = [g.ct_wrap(synth.uniform_mod_device(SEED + 10 + n, f"ct/{n}", list(ps.q[:lv]), ps.n, count=2,
+                                              device=device), lv) for n, (_, _, lv) in enumerate(items)]
+    outs = [g.ct_empty(lv - 1) for (_, _, lv) in items]
+    fs = [mats[(d, st)] for d, st, _ in items]
+    sps = [split_of[(d, st)] for d, st, _ in items]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dist.barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        return dist.max(e0.elapsed_time(e1))
+
+    def sequential():
+        for c, o, f, sp in zip(cts, outs, fs, sps):
+            g.lt_eval(c, f, "th", sp, out=o)
+
+    rec = g.lt_graph(cts, fs, algos=["th"] * n_lt, splits=sps, outs=outs)
+    steps = max(1, min(args.steps, 20))
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    ms_graph = timed(lambda: rec.launch(), steps)
+    ms_seq = timed(sequential, steps)
+    clk = clocks.stop()
+    rec.close()
+    val = dist.world * n_lt * steps / (ms_graph / 1e3)
+    return {
+        "metric": METRIC, "value": round(val, 3), "unit": "LT/s", "n_gpus": dist.world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_graph / steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (uniform residues drawn on the device; seeded)",
+        "config": {"workload": f"uneven batch: {n_lt} LTs, N=2^16, D from {{16,64,256,1024}}, consecutive or "
+                               f"2^k-strided offsets, levels 6..24 (seed 3), one matrix per (D, stride) shape; one "
+                               f"recorded lt_eval_batch per step",
+                   "shapes": {f"{d}/{st}": list(split_of[(d, st)]) for d, st in shapes},
+                   "keys": len(rots)},
+        "sequential_lt_per_s": round(dist.world * n_lt * steps / (ms_seq / 1e3), 3),
+        "speedup_vs_sequential": round(ms_seq / ms_graph, 3),
+        "clocks": clk,
+    }
+
+
 def run_serving(args, dist: Dist):
     """Poisson arrivals (rate, duration; seed 4) of single-LT requests, each with
     N from {2^15, 2^16}, 32..512 diagonals (powers of two) and a level of
@@ -662,6 +749,8 @@ def main():
             res = run_batched(args, dist)
         elif args.workload == "serving":
             res = run_serving(args, dist)
+        elif args.workload == "uneven":
+            res = run_uneven(args, dist)
         else:
             res = run_ours(args, dist)
         if dist.rank == 0 and res is not None:

@@ -91,3 +91,26 @@ def test_recorded_batch_replays_on_new_inputs():
         assert_same(a, b, "replay 2")
     assert not np.array_equal(first[0], second[0])
     rec.close()
+
+
+def test_toy_batch_two_matrices_with_strides():
+    """A batch mixing two matrices (16 diagonals at stride 4, 8 diagonals
+    consecutive) at two levels: every item equals its separate lt_eval."""
+    pa = make_problem("toy", 11, 16, stride=4)
+    pb_ = make_problem("toy", 11, 8)
+    g = gpu_context("toy")
+    for split, pr in [((2, 2, 4), pa), ((2, 2, 2), pb_)]:
+        add_keys(pa, olt.rotation_set("th", pr.D, split, pr.stride, pa.ctx.N // 2))
+    fa = upload_problem(g, pa, stride=4)
+    fb = g.upload_diagonals(pb_.diags, stride=1, level=pb_.ctx.L)
+    levels = [4, 3, 4, 2, 3, 4]
+    cts, _ = _encrypt_many(pa, levels, 300)
+    ins = [g.ct_from_host(np.stack(ct)) for ct in cts]
+    fs = [fa, fb, fa, fb, fa, fb]
+    splits = [(2, 2, 4) if f is fa else (2, 2, 2) for f in fs]
+    outs = g.lt_eval_batch(ins, fs, algos=["th"] * 6, splits=splits)
+    for n in range(6):
+        single, _ = g.lt_eval(ins[n], fs[n], "th", splits[n])
+        assert_same(outs[n].numpy(), single.numpy(), f"item {n}")
+    want = np.stack(olt.lt_th_bsgs(pa.ctx, cts[0], pa.diags, pa.keys, 2, 2, 4, stride=4)[0])
+    assert_same(outs[0].numpy(), want, "strided item vs oracle")
