@@ -117,6 +117,15 @@ ckks_status ckks_upload_diagonals(ckks_ctx* ctx, ckks_diags** out, uint32_t n_di
 ckks_status ckks_upload_diagonals_device(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t offset0,
                                          int32_t stride, uint32_t level, const uint64_t* dev, size_t n_words,
                                          void* stream);
+/* Allocate diagonals without contents (layout as above), to be filled with
+ * ckks_diags_write_device, e.g. in pieces when the whole matrix is too large
+ * to stage twice in device memory. */
+ckks_status ckks_diags_create(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t offset0, int32_t stride,
+                              uint32_t level);
+/* Copy diagonals [first, first + count) from a device buffer
+ * [count][level + k][N] (stream-ordered). */
+ckks_status ckks_diags_write_device(ckks_diags* f, uint32_t first, uint32_t count, const uint64_t* dev,
+                                   size_t n_words, void* stream);
 ckks_status ckks_free_diags(ckks_diags* f);
 
 /* ------------------------------------------------------------------ ciphertexts */

@@ -63,6 +63,8 @@ def lib():
         "ckks_upload_diagonals": [P, PP, U32, I32, I32, U32, P, SZ],
         "ckks_upload_diagonals_device": [P, PP, U32, I32, I32, U32, P, SZ, P],
         "ckks_free_diags": [P],
+        "ckks_diags_create": [P, PP, U32, I32, I32, U32],
+        "ckks_diags_write_device": [P, U32, U32, P, SZ, P],
         "ckks_ct_create": [P, PP, U32],
         "ckks_ct_upload": [P, PP, U32, P],
         "ckks_ct_wrap_device": [P, PP, U32, P],
@@ -268,6 +270,16 @@ class Context:
         check(lib().ckks_upload_diagonals_device(self.h, ctypes.byref(h), diags_t.shape[0], 0, stride, level,
                                                  _ptr(diags_t), diags_t.numel(), _stream(stream)))
         return Diagonals(self, h, diags_t.shape[0], stride, level)
+
+    def diags_create(self, n_diag: int, stride: int = 1, level: int | None = None) -> Diagonals:
+        level = level if level is not None else self.L
+        h = ctypes.c_void_p()
+        check(lib().ckks_diags_create(self.h, ctypes.byref(h), n_diag, 0, stride, level))
+        return Diagonals(self, h, n_diag, stride, level)
+
+    def diags_write(self, f: Diagonals, first: int, chunk_t, stream=None) -> None:
+        check(lib().ckks_diags_write_device(f.handle, first, chunk_t.shape[0], _ptr(chunk_t), chunk_t.numel(),
+                                            _stream(stream)))
 
     def required_rotations(self, algo: str, split, n_diag: int, stride: int = 1) -> list:
         sp = Split(*(tuple(split) + (0,) * (3 - len(split)))) if split else None

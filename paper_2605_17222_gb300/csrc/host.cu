@@ -1100,6 +1100,39 @@ ckks_status ckks_upload_diagonals_device(ckks_ctx* ctx, ckks_diags** out, uint32
     });
 }
 
+ckks_status ckks_diags_create(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t offset0, int32_t stride,
+                              uint32_t level) {
+    return guarded([&] {
+        if (!ctx || !out) fail(CKKS_EINVAL, "null argument");
+        *out = nullptr;
+        if (offset0 != 0) fail(CKKS_EINVAL, "offset0 must be 0");
+        if (stride < 1 || n_diag < 1) fail(CKKS_EINVAL, "need n_diag >= 1 and stride >= 1");
+        if ((u64)stride * (n_diag - 1) >= ctx->slots()) fail(CKKS_EINVAL, "offsets exceed N/2");
+        if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        CK(cudaSetDevice(ctx->device));
+        auto f = std::make_unique<ckks_diags>();
+        f->ctx = ctx;
+        f->n_diag = n_diag;
+        f->level = level;
+        f->offset0 = offset0;
+        f->stride = stride;
+        f->d = ctx->dalloc((size_t)n_diag * (level + ctx->K) * ctx->N);
+        *out = f.release();
+    });
+}
+
+ckks_status ckks_diags_write_device(ckks_diags* f, uint32_t first, uint32_t count, const uint64_t* dev,
+                                   size_t n_words, void* stream) {
+    return guarded([&] {
+        if (!f || !dev) fail(CKKS_EINVAL, "null argument");
+        const size_t per = (size_t)(f->level + f->ctx->K) * f->ctx->N;
+        if ((u64)first + count > f->n_diag) fail(CKKS_EINVAL, "range exceeds n_diag");
+        if (n_words != per * count) fail(CKKS_EINVAL, "size mismatch");
+        CK(cudaSetDevice(f->ctx->device));
+        CK(cudaMemcpyAsync(f->d + per * first, dev, n_words * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    });
+}
+
 ckks_status ckks_free_diags(ckks_diags* f) {
     return guarded([&] {
         if (!f) return;
