@@ -110,7 +110,16 @@ int ckks_has_rotation_key(const ckks_ctx* ctx, int32_t r);
  * Host layout [n_diag][level + k][N]: Q limbs q_0..q_{level-1} then the k P
  * limbs, NTT domain.  `level` is the level the diagonals were encoded at; an
  * LT at a ciphertext level l <= level uses the first l Q limbs and the P
- * limbs.  offset0 must be 0 (EINVAL otherwise). */
+ * limbs.  offset0 lies in (-N/2, N/2) (EINVAL otherwise), stride >= 1 and
+ * stride*(n_diag-1) < N/2, so that the n_diag offsets are distinct mod N/2.
+ * A nonzero offset0 joins the outermost rotation layer of each algorithm:
+ * with g_t = Rot(f_t, -offset0), sum_t f_t . Rot(z, offset0 + stride t) =
+ * Rot(sum_t g_t . Rot(z, stride t), offset0), so the giant (BSGS, DH-BSGS)
+ * or outer (TH-BSGS) amounts become offset0 + stride*n1(*n2)*k for every k,
+ * the first included, and the diagonal method ends with one rotation by
+ * offset0 (one more key, Decompose and ModDown).  An amount that is 0 mod
+ * N/2 needs no key.  Such windows o_t = -m*s .. m*s are the sparse stages of
+ * a factored DFT (CoeffToSlot / SlotToCoeff). */
 ckks_status ckks_upload_diagonals(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t offset0,
                                   int32_t stride, uint32_t level, const uint64_t* host, size_t n_words);
 /* Same, from a device buffer the library copies (stream-ordered on `stream`). */
@@ -168,6 +177,21 @@ ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* i
                           const ckks_diags* const* f, const lt_algo* algos, const lt_split* splits,
                           ckks_ct* const* out, void* stream);
 
+/* A chain of LTs, one level each: the stages of a factored transform such as
+ * the CoeffToSlot / SlotToCoeff DFTs of bootstrapping, the multi-stage sparse
+ * LTs the hoisted algorithms target (Sec. I).  Stage i evaluates LT_{f[i]} at
+ * level in->level - i on the previous stage's output (stage 0 on `in`);
+ * `out` receives the last stage's result, at level in->level - n_stages.
+ * algos/splits: per stage, or NULL for TH-BSGS with the library's split (the
+ * tuned one if lt_autotune ran for that shape).  Every stage is validated --
+ * levels, splits, keys -- before anything is queued.  Intermediate
+ * ciphertexts come from the stream-ordered allocator on `stream` and are
+ * released in stream order.  chosen (may be NULL) receives each stage's
+ * split.  Each stage's residues equal those of a separate lt_eval. */
+ckks_status lt_eval_chain(ckks_ctx* ctx, const ckks_ct* in, uint32_t n_stages, const ckks_diags* const* f,
+                          const lt_algo* algos, const lt_split* splits, ckks_ct* out, void* stream,
+                          lt_split* chosen);
+
 /* A recorded batch.  lt_graph_create runs lt_eval_batch once with these
  * arguments (which also sets up every table the batch needs), then records
  * the same work into a CUDA graph; lt_graph_launch replays it on `stream`,
@@ -185,7 +209,8 @@ ckks_status lt_graph_destroy(lt_graph* graph);
  * algorithm needs for n_diag diagonals and this split; returns how many were
  * written (at most cap), or -1 on a bad split. */
 int32_t lt_required_rotations(const ckks_ctx* ctx, lt_algo algo, const lt_split* split,
-                              uint32_t n_diag, int32_t stride, int32_t* rot_out, uint32_t cap);
+                              uint32_t n_diag, int32_t offset0, int32_t stride, int32_t* rot_out,
+                              uint32_t cap);
 
 /* The cost model's ranking of the admissible splits for (algo, level,
  * n_diag), fastest first; writes at most cap and returns how many. */
@@ -196,7 +221,7 @@ int32_t lt_candidate_splits(const ckks_ctx* ctx, lt_algo algo, uint32_t level, u
  * split of f's n_diag for `algo` with the library's cost model, keeps the
  * first max_candidates whose rotation keys are all uploaded, times each on
  * `sample` (its level and f's stride define the shape), and records the
- * fastest for that (algo, level, n_diag, stride); lt_eval and lt_eval_batch
+ * fastest for that (algo, level, n_diag, stride, offset0); lt_eval and lt_eval_batch
  * then use it whenever no split is given.  Synchronous; allocates one scratch
  * ciphertext.  ENOKEY if no candidate has all of its keys. */
 ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, const ckks_diags* f,

@@ -74,6 +74,7 @@ def lib():
         "ckks_free_ct": [P],
         "lt_eval": [P, P, P, I, P, P, P, P],
         "lt_eval_batch": [P, U32, P, P, P, P, P, P],
+        "lt_eval_chain": [P, P, U32, P, P, P, P, P, P],
         "lt_choose_split": [P, I, U32, U32, P],
         "lt_autotune": [P, I, P, P, U32, P, P],
         "ckks_poly_ntt": [P, P, U32, I, I, P],
@@ -99,7 +100,7 @@ def lib():
     L.ckks_kernel_launch_count.restype = ctypes.c_uint64
     L.ckks_has_rotation_key.argtypes = [P, I32]
     L.ckks_has_rotation_key.restype = I
-    L.lt_required_rotations.argtypes = [P, I, P, U32, I32, P, U32]
+    L.lt_required_rotations.argtypes = [P, I, P, U32, I32, I32, P, U32]
     L.lt_required_rotations.restype = I32
     L.ckks_ct_level.argtypes = [P]
     L.ckks_ct_level.restype = U32
@@ -179,8 +180,11 @@ class Ciphertext:
 
 
 class Diagonals:
-    def __init__(self, ctx, handle, n_diag, stride, level):
+    """Encoded diagonals on the device; offsets offset0 + stride * t, t < n_diag."""
+
+    def __init__(self, ctx, handle, n_diag, stride, level, offset0=0):
         self.ctx, self.handle, self.n_diag, self.stride, self.level = ctx, handle, n_diag, stride, level
+        self.offset0 = offset0
 
     def free(self):
         if self.handle:
@@ -255,37 +259,39 @@ class Context:
     def has_key(self, r: int) -> bool:
         return bool(lib().ckks_has_rotation_key(self.h, int(r)))
 
-    def upload_diagonals(self, diags: np.ndarray, stride: int = 1, level: int | None = None) -> Diagonals:
+    def upload_diagonals(self, diags: np.ndarray, stride: int = 1, level: int | None = None,
+                         offset0: int = 0) -> Diagonals:
         diags = np.ascontiguousarray(diags, dtype=np.uint64)
         level = level if level is not None else diags.shape[1] - self.k
         h = ctypes.c_void_p()
-        check(lib().ckks_upload_diagonals(self.h, ctypes.byref(h), diags.shape[0], 0, stride, level,
+        check(lib().ckks_upload_diagonals(self.h, ctypes.byref(h), diags.shape[0], offset0, stride, level,
                                           _ptr(diags), diags.size))
-        return Diagonals(self, h, diags.shape[0], stride, level)
+        return Diagonals(self, h, diags.shape[0], stride, level, offset0)
 
-    def upload_diagonals_device(self, diags_t, stride: int = 1, level: int | None = None, stream=None) -> Diagonals:
+    def upload_diagonals_device(self, diags_t, stride: int = 1, level: int | None = None, stream=None,
+                                offset0: int = 0) -> Diagonals:
         """diags_t: device tensor [n_diag][level + k][N] (copied by the library)."""
         level = level if level is not None else diags_t.shape[1] - self.k
         h = ctypes.c_void_p()
-        check(lib().ckks_upload_diagonals_device(self.h, ctypes.byref(h), diags_t.shape[0], 0, stride, level,
+        check(lib().ckks_upload_diagonals_device(self.h, ctypes.byref(h), diags_t.shape[0], offset0, stride, level,
                                                  _ptr(diags_t), diags_t.numel(), _stream(stream)))
-        return Diagonals(self, h, diags_t.shape[0], stride, level)
+        return Diagonals(self, h, diags_t.shape[0], stride, level, offset0)
 
-    def diags_create(self, n_diag: int, stride: int = 1, level: int | None = None) -> Diagonals:
+    def diags_create(self, n_diag: int, stride: int = 1, level: int | None = None, offset0: int = 0) -> Diagonals:
         level = level if level is not None else self.L
         h = ctypes.c_void_p()
-        check(lib().ckks_diags_create(self.h, ctypes.byref(h), n_diag, 0, stride, level))
-        return Diagonals(self, h, n_diag, stride, level)
+        check(lib().ckks_diags_create(self.h, ctypes.byref(h), n_diag, offset0, stride, level))
+        return Diagonals(self, h, n_diag, stride, level, offset0)
 
     def diags_write(self, f: Diagonals, first: int, chunk_t, stream=None) -> None:
         check(lib().ckks_diags_write_device(f.handle, first, chunk_t.shape[0], _ptr(chunk_t), chunk_t.numel(),
                                             _stream(stream)))
 
-    def required_rotations(self, algo: str, split, n_diag: int, stride: int = 1) -> list:
+    def required_rotations(self, algo: str, split, n_diag: int, stride: int = 1, offset0: int = 0) -> list:
         sp = Split(*(tuple(split) + (0,) * (3 - len(split)))) if split else None
         buf = (ctypes.c_int32 * 4096)()
-        n = lib().lt_required_rotations(self.h, ALGOS[algo], ctypes.byref(sp) if sp else None, n_diag, stride,
-                                        buf, 4096)
+        n = lib().lt_required_rotations(self.h, ALGOS[algo], ctypes.byref(sp) if sp else None, n_diag, offset0,
+                                        stride, buf, 4096)
         if n < 0:
             raise CkksError(1, "bad split")
         return list(buf[:n])
@@ -367,6 +373,18 @@ class Context:
             sp = (Split * n)(*[Split(*(tuple(s) + (1,) * (3 - len(s)))) for s in splits])
         check(lib().lt_eval_batch(self.h, n, arr(cts), arr(diags), al, sp, arr(outs), _stream(stream)))
         return outs
+
+    def lt_eval_chain(self, ct, stages, algos=None, splits=None, out=None, stream=None):
+        """A chain of LTs (lt_eval_chain): stage i applies stages[i] at level
+        ct.level - i; returns (output at ct.level - len(stages), chosen splits)."""
+        n = len(stages)
+        out = out or self.ct_empty(ct.level - n)
+        fs = (ctypes.c_void_p * n)(*[f.handle for f in stages])
+        al = (ctypes.c_int * n)(*[ALGOS[a] for a in algos]) if algos else None
+        sp = (Split * n)(*[Split(*(tuple(x) + (1,) * (3 - len(x)))) for x in splits]) if splits else None
+        chosen = (Split * n)()
+        check(lib().lt_eval_chain(self.h, ct.handle, n, fs, al, sp, out.handle, _stream(stream), chosen))
+        return out, [c.tuple() for c in chosen]
 
     def lt_graph(self, cts, diags, algos=None, splits=None, outs=None):
         """Record one lt_eval_batch into a replayable graph (see lt_graph_create)."""

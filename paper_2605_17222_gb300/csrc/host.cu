@@ -137,7 +137,7 @@ struct ckks_ctx {
     NttTables T{};
     std::map<u32, LevelConsts> levels;
     std::map<u32, u64*> keys;  // rotation (mod N/2) -> [beta_max][2][L+K][N]
-    std::map<std::tuple<int, u32, u32, int32_t>, lt_split> tuned;  // (algo, level, D, stride) -> measured best
+    std::map<std::tuple<int, u32, u32, int32_t, int32_t>, lt_split> tuned;  // (algo, level, D, stride, offset0 mod N/2)
     std::mutex mu;
     size_t bytes = 0;
 
@@ -461,6 +461,29 @@ struct LtIO {
     u64* o1;
 };
 
+// The outermost rotation layer of a schedule: amounts offset0 + stride * step * k
+// (mod N/2) for k < count.  Offsets o_t = offset0 + stride t give
+//   sum_t f_t . Rot(z, o_t) = sum_k Rot( sum_t' f^_t' . Rot(z, stride t'), amount_k )
+// with f^ = Rot(f, -amount_k), so the base offset0 joins this layer (every k,
+// the first included).  An amount of 0 needs no key; at most one k has it,
+// since the amounts differ by nonzero multiples of stride * step below N/2.
+struct OuterLayer {
+    std::vector<int64_t> amount;  // in [0, N/2)
+    std::vector<u32> rotated;     // the k with a nonzero amount, ascending
+    int identity = -1;            // the k with amount 0, or -1
+};
+
+OuterLayer outer_layer(const ckks_ctx* C, const ckks_diags* f, int64_t step, u32 count) {
+    OuterLayer o;
+    for (u32 k = 0; k < count; k++) {
+        const int64_t r = C->rotkey((int64_t)f->offset0 + (int64_t)f->stride * step * k);
+        o.amount.push_back(r);
+        if (r) o.rotated.push_back(k);
+        else if (o.identity < 0) o.identity = (int)k;
+    }
+    return o;
+}
+
 // TH-BSGS, Algorithm 2 (n1, n2, n3 = n'1, n'2, n'3).  DH-BSGS (Algorithm 1)
 // is the case n1 = 1 with (n2, n3) = (n1, n2) of Algorithm 1, and the hoisted
 // diagonal method the case (1, D, 1): the three share this schedule and give
@@ -469,7 +492,7 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
     const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
     const int64_t s = f->stride;
     Arena ar(st, N);
-    const u32 nb = std::max<u32>(1, std::max(n1 - 1, n3 - 1));  // widest batch of the key-switch phases
+    const u32 nb = std::max<u32>(1, std::max(n1 - 1, n3));  // widest batch of the key-switch phases
     u64* Y = ar.limbs(std::max<size_t>((size_t)nb * level, 2 * (C->K + 1)));
     std::vector<u64*> A(n1, nullptr), B(n1, nullptr), Dg(n1, nullptr);
     Dg[0] = ar.limbs((size_t)beta * ext);
@@ -508,19 +531,27 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
         a.keys[j] = key_of(C, s * n1 * j);
         a.gal_mid[j] = C->galois(s * n1 * j);
     }
+    const OuterLayer ol = outer_layer(C, f, (int64_t)n1 * n2, n3);
     std::vector<u64*> U0(n3), U1(n3);
     for (u32 k = 0; k < n3; k++) {
         U0[k] = ar.limbs(ext);
         U1[k] = ar.limbs(ext);
         a.U0[k] = U0[k];
         a.U1[k] = U1[k];
-        a.gal_diag[k] = k ? C->galois(-s * n1 * n2 * k) : 0;
+        a.gal_diag[k] = ol.amount[k] ? C->galois(-ol.amount[k]) : 0;
     }
     launch_diag_mac(a, st);  // lines 8-14
-    if (n3 > 1) {            // lines 15-18 for every k at once
+    // the accumulator: the partial sum whose outer amount is 0, else zeros
+    u64* acc0 = ol.identity >= 0 ? U0[ol.identity] : ar.limbs(ext);
+    u64* acc1 = ol.identity >= 0 ? U1[ol.identity] : ar.limbs(ext);
+    if (ol.identity < 0) {
+        CK(cudaMemsetAsync(acc0, 0, (size_t)ext * N * sizeof(u64), st));
+        CK(cudaMemsetAsync(acc1, 0, (size_t)ext * N * sizeof(u64), st));
+    }
+    if (!ol.rotated.empty()) {  // lines 15-18 for every rotated k at once
         std::vector<const u64*> us, tqc;
         std::vector<u64*> tq, dk;
-        for (u32 k = 1; k < n3; k++) {
+        for (u32 k : ol.rotated) {
             us.push_back(U1[k]);
             tq.push_back(ar.limbs(level));
             tqc.push_back(tq.back());
@@ -528,20 +559,19 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
         }
         op_moddown_batch(C, level, us, tq, Y, st);
         op_decompose_batch(C, level, tqc, 0, dk, Y, st);
-        for (u32 k0 = 1; k0 < n3; k0 += KS_MAX_MULTI) {
+        for (size_t c0 = 0; c0 < ol.rotated.size(); c0 += KS_MAX_MULTI) {
             KsMultiArgs m;
             memset(&m, 0, sizeof(m));
-            m.count = std::min<u32>(KS_MAX_MULTI, n3 - k0);
+            m.count = (u32)std::min<size_t>(KS_MAX_MULTI, ol.rotated.size() - c0);
             for (u32 c = 0; c < m.count; c++) {
-                const u32 k = k0 + c;
-                const int64_t r = s * n1 * n2 * k;
-                m.digits[c] = dk[k - 1];
-                m.keys[c] = key_of(C, r);
+                const u32 k = ol.rotated[c0 + c];
+                m.digits[c] = dk[c0 + c];
+                m.keys[c] = key_of(C, ol.amount[k]);
                 m.x0[c] = U0[k];
-                m.gal[c] = C->galois(r);
+                m.gal[c] = C->galois(ol.amount[k]);
             }
-            m.out0 = U0[0];
-            m.out1 = U1[0];
+            m.out0 = acc0;
+            m.out1 = acc1;
             m.mods = (const ModC*)C->d_mods.p;
             m.level = level;
             m.ext = ext;
@@ -551,7 +581,7 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
             launch_ks_multi(m, st);
         }
     }
-    op_moddown_rescale_batch(C, level, std::vector<const u64*>{U0[0], U1[0]}, std::vector<u64*>{io.o0, io.o1}, Y,
+    op_moddown_rescale_batch(C, level, std::vector<const u64*>{acc0, acc1}, std::vector<u64*>{io.o0, io.o1}, Y,
                              st);  // line 19
 }
 
@@ -569,7 +599,7 @@ void sched_th_batch(ckks_ctx* C, u32 level, const std::vector<LtIO>& ios, const 
     const size_t dig = (size_t)beta * ext;  // limbs of one digit set
     const int64_t s = f->stride;
     Arena ar(st, N);
-    const u32 nb = std::max<u32>(1, std::max(n1 - 1, n3 - 1)) * nbat;
+    const u32 nb = std::max<u32>(1, std::max(n1 - 1, n3)) * nbat;
     u64* Y = ar.limbs(std::max<size_t>((size_t)std::max(nb, nbat) * level, 2ull * nbat * (C->K + 1)));
     u64* Aall = ar.limbs((size_t)nbat * n1 * ext);  // [b][i][ext]; i = 0 unused (lifted input)
     u64* Ball = ar.limbs((size_t)nbat * n1 * ext);
@@ -636,17 +666,28 @@ void sched_th_batch(ckks_ctx* C, u32 level, const std::vector<LtIO>& ios, const 
         a.keys[j] = key_of(C, s * n1 * j);
         a.gal_mid[j] = C->galois(s * n1 * j);
     }
+    const OuterLayer ol = outer_layer(C, f, (int64_t)n1 * n2, n3);
     for (u32 k = 0; k < n3; k++) {
         a.U0[k] = Up(0, k, 0);
         a.U1[k] = Up(0, k, 1);
-        a.gal_diag[k] = k ? C->galois(-s * n1 * n2 * k) : 0;
+        a.gal_diag[k] = ol.amount[k] ? C->galois(-ol.amount[k]) : 0;
     }
     launch_diag_mac(a, st);  // lines 8-14
-    if (n3 > 1) {            // lines 15-18
+    // per ciphertext: the accumulator is its partial sum with outer amount 0, else zeros
+    u64* Zall = nullptr;
+    if (ol.identity < 0) {
+        Zall = ar.limbs((size_t)nbat * 2 * ext);
+        CK(cudaMemsetAsync(Zall, 0, (size_t)nbat * 2 * ext * N * sizeof(u64), st));
+    }
+    auto Acc = [&](u32 b, u32 c) {
+        return ol.identity >= 0 ? Up(b, (u32)ol.identity, c) : Zall + ((size_t)b * 2 + c) * ext * N;
+    };
+    const size_t nrot = ol.rotated.size();
+    if (nrot) {  // lines 15-18
         std::vector<const u64*> us, tqc;
         std::vector<u64*> tq, dk;
         for (u32 b = 0; b < nbat; b++)
-            for (u32 k = 1; k < n3; k++) {
+            for (u32 k : ol.rotated) {
                 us.push_back(Up(b, k, 1));
                 tq.push_back(ar.limbs(level));
                 tqc.push_back(tq.back());
@@ -655,20 +696,19 @@ void sched_th_batch(ckks_ctx* C, u32 level, const std::vector<LtIO>& ios, const 
         op_moddown_batch(C, level, us, tq, Y, st);
         op_decompose_batch(C, level, tqc, 0, dk, Y, st);
         for (u32 b = 0; b < nbat; b++)
-            for (u32 k0 = 1; k0 < n3; k0 += KS_MAX_MULTI) {
+            for (size_t c0 = 0; c0 < nrot; c0 += KS_MAX_MULTI) {
                 KsMultiArgs m;
                 memset(&m, 0, sizeof(m));
-                m.count = std::min<u32>(KS_MAX_MULTI, n3 - k0);
+                m.count = (u32)std::min<size_t>(KS_MAX_MULTI, nrot - c0);
                 for (u32 c = 0; c < m.count; c++) {
-                    const u32 k = k0 + c;
-                    const int64_t r = s * n1 * n2 * k;
-                    m.digits[c] = dk[(size_t)b * (n3 - 1) + (k - 1)];
-                    m.keys[c] = key_of(C, r);
+                    const u32 k = ol.rotated[c0 + c];
+                    m.digits[c] = dk[(size_t)b * nrot + c0 + c];
+                    m.keys[c] = key_of(C, ol.amount[k]);
                     m.x0[c] = Up(b, k, 0);
-                    m.gal[c] = C->galois(r);
+                    m.gal[c] = C->galois(ol.amount[k]);
                 }
-                m.out0 = Up(b, 0, 0);
-                m.out1 = Up(b, 0, 1);
+                m.out0 = Acc(b, 0);
+                m.out1 = Acc(b, 1);
                 m.mods = (const ModC*)C->d_mods.p;
                 m.level = level;
                 m.ext = ext;
@@ -681,9 +721,9 @@ void sched_th_batch(ckks_ctx* C, u32 level, const std::vector<LtIO>& ios, const 
     std::vector<const u64*> xs;
     std::vector<u64*> outs;
     for (u32 b = 0; b < nbat; b++) {
-        xs.push_back(Up(b, 0, 0));
+        xs.push_back(Acc(b, 0));
         outs.push_back(ios[b].o0);
-        xs.push_back(Up(b, 0, 1));
+        xs.push_back(Acc(b, 1));
         outs.push_back(ios[b].o1);
     }
     op_moddown_rescale_batch(C, level, xs, outs, Y, st);  // line 19
@@ -727,18 +767,25 @@ void sched_bsgs(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u3
         a.A[i] = c0;
         a.B[i] = c1;
     }
+    const OuterLayer ol = outer_layer(C, f, n1, n2);
     std::vector<u64*> V0(n2), V1(n2);
     for (u32 j = 0; j < n2; j++) {
         V0[j] = ar.limbs(level);
         V1[j] = ar.limbs(level);
         a.U0[j] = V0[j];
         a.U1[j] = V1[j];
-        a.gal_diag[j] = j ? C->galois(-s * n1 * j) : 0;
+        a.gal_diag[j] = ol.amount[j] ? C->galois(-ol.amount[j]) : 0;
     }
     launch_diag_mac(a, st);
-    for (u32 j = 1; j < n2; j++) rotate_into(V0[j], V1[j], s * n1 * j, V0[0], V1[0], 1);
-    op_rescale(C, level, V0[0], io.o0, Y, st);
-    op_rescale(C, level, V1[0], io.o1, Y, st);
+    u64* acc0 = ol.identity >= 0 ? V0[ol.identity] : ar.limbs(level);
+    u64* acc1 = ol.identity >= 0 ? V1[ol.identity] : ar.limbs(level);
+    if (ol.identity < 0) {
+        CK(cudaMemsetAsync(acc0, 0, (size_t)level * N * sizeof(u64), st));
+        CK(cudaMemsetAsync(acc1, 0, (size_t)level * N * sizeof(u64), st));
+    }
+    for (u32 j : ol.rotated) rotate_into(V0[j], V1[j], ol.amount[j], acc0, acc1, 1);
+    op_rescale(C, level, acc0, io.o0, Y, st);
+    op_rescale(C, level, acc1, io.o1, Y, st);
 }
 
 void validate_split(lt_algo algo, u32 D, const lt_split& sp) {
@@ -761,19 +808,31 @@ void validate_split(lt_algo algo, u32 D, const lt_split& sp) {
     if (algo == LT_DIAG && D > (u32)DM_MAX_N2) fail(CKKS_EINVAL, "too many diagonals for the diagonal method");
 }
 
-std::vector<int64_t> rotations(lt_algo algo, const lt_split& sp, u32 D) {
+// Rotation amounts (in [1, N/2)) whose keys an LT over offsets
+// offset0 + stride t needs with this split; the outermost layer carries offset0.
+std::vector<int64_t> rotations(const ckks_ctx* C, lt_algo algo, const lt_split& sp, u32 D, int64_t stride,
+                               int64_t offset0) {
     std::vector<int64_t> r;
+    auto add = [&](int64_t x) {
+        x = C->rotkey(x);
+        if (x) r.push_back(x);
+    };
     if (algo == LT_DIAG) {
-        for (u32 t = 1; t < D; t++) r.push_back(t);
+        for (u32 t = 1; t < D; t++) add(stride * t);
+        add(offset0);
     } else if (algo == LT_BSGS || algo == LT_DH_BSGS) {
-        for (u32 i = 1; i < sp.n1; i++) r.push_back(i);
-        for (u32 j = 1; j < sp.n2; j++) r.push_back((int64_t)sp.n1 * j);
+        for (u32 i = 1; i < sp.n1; i++) add(stride * i);
+        for (u32 j = 0; j < sp.n2; j++) add(offset0 + stride * sp.n1 * j);
     } else {
-        for (u32 i = 1; i < sp.n1; i++) r.push_back(i);
-        for (u32 j = 1; j < sp.n2; j++) r.push_back((int64_t)sp.n1 * j);
-        for (u32 k = 1; k < sp.n3; k++) r.push_back((int64_t)sp.n1 * sp.n2 * k);
+        for (u32 i = 1; i < sp.n1; i++) add(stride * i);
+        for (u32 j = 1; j < sp.n2; j++) add(stride * sp.n1 * j);
+        for (u32 k = 0; k < sp.n3; k++) add(offset0 + stride * sp.n1 * sp.n2 * k);
     }
     return r;
+}
+
+std::vector<int64_t> rotations(const ckks_ctx* C, lt_algo algo, const lt_split& sp, const ckks_diags* f) {
+    return rotations(C, algo, sp, f->n_diag, f->stride, f->offset0);
 }
 
 }  // namespace
@@ -848,11 +907,12 @@ static std::vector<lt_split> ranked_splits(const ckks_ctx* C, lt_algo algo, u32 
     return out;
 }
 
-static lt_split choose_split(const ckks_ctx* C, lt_algo algo, u32 level, u32 D, int32_t stride = 1) {
+static lt_split choose_split(const ckks_ctx* C, lt_algo algo, u32 level, u32 D, int32_t stride = 1,
+                             int32_t offset0 = 0) {
     if (algo == LT_DIAG) return lt_split{1, D, 1};
     {
         std::lock_guard<std::mutex> g(const_cast<ckks_ctx*>(C)->mu);
-        auto it = C->tuned.find(std::make_tuple((int)algo, level, D, stride));
+        auto it = C->tuned.find(std::make_tuple((int)algo, level, D, stride, (int32_t)C->rotkey(offset0)));
         if (it != C->tuned.end()) return it->second;
     }
     std::vector<lt_split> r = ranked_splits(C, algo, level, D);
@@ -1066,7 +1126,8 @@ static void put_diags(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, int32_t 
                       uint32_t level, const uint64_t* host, size_t n_words, cudaMemcpyKind kind, cudaStream_t st) {
         if (!ctx || !out || !host) fail(CKKS_EINVAL, "null argument");
         *out = nullptr;
-        if (offset0 != 0) fail(CKKS_EINVAL, "offset0 must be 0");
+        if (offset0 <= -(int64_t)ctx->slots() || offset0 >= (int64_t)ctx->slots())
+            fail(CKKS_EINVAL, "offset0 must lie in (-N/2, N/2)");
         if (stride < 1 || n_diag < 1) fail(CKKS_EINVAL, "need n_diag >= 1 and stride >= 1");
         if ((u64)stride * (n_diag - 1) >= ctx->slots()) fail(CKKS_EINVAL, "offsets exceed N/2");
         if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
@@ -1105,7 +1166,8 @@ ckks_status ckks_diags_create(ckks_ctx* ctx, ckks_diags** out, uint32_t n_diag, 
     return guarded([&] {
         if (!ctx || !out) fail(CKKS_EINVAL, "null argument");
         *out = nullptr;
-        if (offset0 != 0) fail(CKKS_EINVAL, "offset0 must be 0");
+        if (offset0 <= -(int64_t)ctx->slots() || offset0 >= (int64_t)ctx->slots())
+            fail(CKKS_EINVAL, "offset0 must lie in (-N/2, N/2)");
         if (stride < 1 || n_diag < 1) fail(CKKS_EINVAL, "need n_diag >= 1 and stride >= 1");
         if ((u64)stride * (n_diag - 1) >= ctx->slots()) fail(CKKS_EINVAL, "offsets exceed N/2");
         if (level < 1 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
@@ -1210,7 +1272,7 @@ ckks_status ckks_free_ct(ckks_ct* ct) {
 }
 
 int32_t lt_required_rotations(const ckks_ctx* ctx, lt_algo algo, const lt_split* split, uint32_t n_diag,
-                              int32_t stride, int32_t* rot_out, uint32_t cap) {
+                              int32_t offset0, int32_t stride, int32_t* rot_out, uint32_t cap) {
     if (!ctx) return -1;
     lt_split sp = split ? *split : lt_split{0, 0, 0};
     if (algo == LT_DIAG) sp = lt_split{1, n_diag, 1};
@@ -1221,7 +1283,7 @@ int32_t lt_required_rotations(const ckks_ctx* ctx, lt_algo algo, const lt_split*
         return -1;
     }
     std::vector<u32> rs;
-    for (int64_t r : rotations(algo, sp, n_diag)) rs.push_back(ctx->rotkey(r * stride));
+    for (int64_t r : rotations(ctx, algo, sp, n_diag, stride, offset0)) rs.push_back((u32)r);
     std::sort(rs.begin(), rs.end());
     rs.erase(std::unique(rs.begin(), rs.end()), rs.end());
     u32 n = 0;
@@ -1261,8 +1323,8 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
         std::vector<lt_split> cand;
         for (const lt_split& sp : ranked_splits(ctx, algo, level, D)) {
             bool ok = true;
-            for (int64_t r : rotations(algo, sp, D))
-                if (!ctx->keys.count(ctx->rotkey(r * f->stride))) ok = false;
+            for (int64_t r : rotations(ctx, algo, sp, f))
+                if (!ctx->keys.count(ctx->rotkey(r))) ok = false;
             if (ok) cand.push_back(sp);
             if (cand.size() >= std::max<u32>(1, max_candidates)) break;
         }
@@ -1286,7 +1348,7 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
         }
         {
             std::lock_guard<std::mutex> g(ctx->mu);
-            ctx->tuned[std::make_tuple((int)algo, level, D, f->stride)] = bsp;
+            ctx->tuned[std::make_tuple((int)algo, level, D, f->stride, (int32_t)ctx->rotkey(f->offset0))] = bsp;
         }
         if (chosen) *chosen = bsp;
         if (best_ms) *best_ms = best;
@@ -1309,6 +1371,30 @@ ckks_status lt_choose_split(ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_
     });
 }
 
+// The split an LT of f at `level` runs with (the given one, else the tuned or
+// modelled choice), validated, with every rotation key it needs present.
+static lt_split resolve_split(ckks_ctx* ctx, u32 level, const ckks_diags* f, lt_algo algo, const lt_split* split) {
+    const u32 D = f->n_diag;
+    lt_split sp = (split && (split->n1 || split->n2 || split->n3))
+                      ? *split
+                      : choose_split(ctx, algo, level, D, f->stride, f->offset0);
+    if (algo == LT_DIAG) sp = lt_split{1, D, 1};
+    if (algo != LT_TH_BSGS && sp.n3 == 0) sp.n3 = 1;
+    validate_split(algo, D, sp);
+    for (int64_t r : rotations(ctx, algo, sp, f)) key_of(ctx, r);
+    return sp;
+}
+
+static void dispatch(ckks_ctx* ctx, u32 level, const LtIO& io, const ckks_diags* f, lt_algo algo, const lt_split& sp,
+                     cudaStream_t st) {
+    switch (algo) {
+        case LT_TH_BSGS: sched_th(ctx, level, io, f, sp.n1, sp.n2, sp.n3, st); break;
+        case LT_DH_BSGS: sched_th(ctx, level, io, f, sp.n1, 1, sp.n2, st); break;
+        case LT_DIAG: sched_th(ctx, level, io, f, 1, f->n_diag, 1, st); break;
+        case LT_BSGS: sched_bsgs(ctx, level, io, f, sp.n1, sp.n2, st); break;
+    }
+}
+
 static void lt_eval_impl(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_algo algo, const lt_split* split,
                          ckks_ct* out, cudaStream_t st, lt_split* chosen) {
     if (!ctx || !in || !f || !out) fail(CKKS_EINVAL, "null argument");
@@ -1318,23 +1404,11 @@ static void lt_eval_impl(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, 
     if (level > f->level) fail(CKKS_EINVAL, "diagonals encoded below the ciphertext level");
     if (out->level != level - 1) fail(CKKS_EINVAL, "output level must be input level - 1");
     if (out->d == in->d) fail(CKKS_EINVAL, "output must not alias input");
-    const u32 D = f->n_diag;
-    lt_split sp = (split && (split->n1 || split->n2 || split->n3)) ? *split
-                                                                   : choose_split(ctx, algo, level, D, f->stride);
-    if (algo == LT_DIAG) sp = lt_split{1, D, 1};
-    if (algo != LT_TH_BSGS && sp.n3 == 0) sp.n3 = 1;
-    validate_split(algo, D, sp);
-    for (int64_t r : rotations(algo, sp, D)) key_of(ctx, r * f->stride);
+    const lt_split sp = resolve_split(ctx, level, f, algo, split);
     if (chosen) *chosen = sp;
     CK(cudaSetDevice(ctx->device));
     const size_t lw = (size_t)level * ctx->N;
-    LtIO io{in->d, in->d + lw, out->d, out->d + (size_t)(level - 1) * ctx->N};
-    switch (algo) {
-        case LT_TH_BSGS: sched_th(ctx, level, io, f, sp.n1, sp.n2, sp.n3, st); break;
-        case LT_DH_BSGS: sched_th(ctx, level, io, f, sp.n1, 1, sp.n2, st); break;
-        case LT_DIAG: sched_th(ctx, level, io, f, 1, D, 1, st); break;
-        case LT_BSGS: sched_bsgs(ctx, level, io, f, sp.n1, sp.n2, st); break;
-    }
+    dispatch(ctx, level, LtIO{in->d, in->d + lw, out->d, out->d + (size_t)(level - 1) * ctx->N}, f, algo, sp, st);
     CK(cudaGetLastError());
 }
 
@@ -1351,14 +1425,7 @@ static lt_split batch_item_split(ckks_ctx* ctx, const ckks_ct* in, const ckks_di
     const u32 level = in->level;
     if (level < 2 || level > f->level || out->level != level - 1) fail(CKKS_EINVAL, "bad levels in the batch");
     if (out->d == in->d) fail(CKKS_EINVAL, "output must not alias input");
-    const u32 D = f->n_diag;
-    lt_split sp = (split && (split->n1 || split->n2 || split->n3)) ? *split
-                                                                   : choose_split(ctx, algo, level, D, f->stride);
-    if (algo == LT_DIAG) sp = lt_split{1, D, 1};
-    if (algo != LT_TH_BSGS && sp.n3 == 0) sp.n3 = 1;
-    validate_split(algo, D, sp);
-    for (int64_t r : rotations(algo, sp, D)) key_of(ctx, r * f->stride);
-    return sp;
+    return resolve_split(ctx, level, f, algo, split);
 }
 
 ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* in, const ckks_diags* const* f,
@@ -1407,6 +1474,42 @@ ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* i
             sched_th_batch(ctx, in[ia.idx]->level, group, f[ia.idx], n1, n2, n3, st);
         }
         CK(cudaGetLastError());
+    });
+}
+
+ckks_status lt_eval_chain(ckks_ctx* ctx, const ckks_ct* in, uint32_t n_stages, const ckks_diags* const* f,
+                          const lt_algo* algos, const lt_split* splits, ckks_ct* out, void* stream, lt_split* chosen) {
+    return guarded([&] {
+        if (!ctx || !in || !out || !f) fail(CKKS_EINVAL, "null argument");
+        if (n_stages < 1) fail(CKKS_EINVAL, "need at least one stage");
+        if (in->ctx != ctx || out->ctx != ctx) fail(CKKS_EINVAL, "objects of another context");
+        if (in->level < n_stages + 1) fail(CKKS_EINVAL, "input level too low for the chain (one level per stage)");
+        if (out->level != in->level - n_stages) fail(CKKS_EINVAL, "output level must be input level - n_stages");
+        if (out->d == in->d) fail(CKKS_EINVAL, "output must not alias input");
+        // validate every stage before queuing anything
+        std::vector<lt_split> sp(n_stages);
+        std::vector<lt_algo> al(n_stages);
+        for (u32 i = 0; i < n_stages; i++) {
+            if (!f[i] || f[i]->ctx != ctx) fail(CKKS_EINVAL, "stage diagonals missing or of another context");
+            const u32 level = in->level - i;
+            if (level > f[i]->level) fail(CKKS_EINVAL, "stage diagonals encoded below the stage's level");
+            al[i] = algos ? algos[i] : LT_TH_BSGS;
+            sp[i] = resolve_split(ctx, level, f[i], al[i], splits ? &splits[i] : nullptr);
+        }
+        CK(cudaSetDevice(ctx->device));
+        cudaStream_t st = (cudaStream_t)stream;
+        Arena ar(st, ctx->N);  // the intermediate ciphertexts, freed in stream order after the chain
+        const u64* c = in->d;
+        for (u32 i = 0; i < n_stages; i++) {
+            const u32 level = in->level - i;
+            u64* o = (i + 1 == n_stages) ? out->d : ar.limbs(2ull * (level - 1));
+            dispatch(ctx, level, LtIO{c, c + (size_t)level * ctx->N, o, o + (size_t)(level - 1) * ctx->N}, f[i],
+                     al[i], sp[i], st);
+            c = o;
+        }
+        CK(cudaGetLastError());
+        if (chosen)
+            for (u32 i = 0; i < n_stages; i++) chosen[i] = sp[i];
     });
 }
 

@@ -13,20 +13,31 @@ def gpu_context(param_name: str):
     return binding.Context.from_params(synth.param_set(param_name))
 
 
-def upload_problem(gctx, pb, stride=1):
-    for r, key in pb.keys.items():
+def upload_keys(gctx, keys):
+    for r, key in keys.items():
         if not gctx.has_key(r):
             gctx.upload_rotation_key(r, key)
-    return gctx.upload_diagonals(pb.diags, stride=stride, level=pb.ctx.L)
+
+
+def upload_problem(gctx, pb, stride=1):
+    upload_keys(gctx, pb.keys)
+    return gctx.upload_diagonals(pb.diags, stride=stride, level=pb.ctx.L, offset0=pb.offset0)
+
+
+def upload_chain(gctx, cp):
+    """A ChainProblem's keys and one Diagonals per stage window."""
+    upload_keys(gctx, cp.keys)
+    return [gctx.upload_diagonals(d, stride=w.stride, level=cp.ctx.L, offset0=w.offset0)
+            for d, w in zip(cp.diags, cp.windows)]
 
 
 def oracle_lt(pb, algo, split):
-    ct, _ = olt.run(pb.ctx, algo, pb.ct, pb.diags, pb.keys, split, pb.stride)
+    ct, _ = olt.run(pb.ctx, algo, pb.ct, pb.diags, pb.keys, split, pb.stride, pb.offset0)
     return np.stack(ct)
 
 
 def ensure_keys(pb, algo, split):
-    add_keys(pb, olt.rotation_set(algo, pb.D, split, pb.stride, pb.ctx.N // 2))
+    add_keys(pb, olt.rotation_set(algo, pb.D, split, pb.stride, pb.ctx.N // 2, pb.offset0))
 
 
 def assert_same(got: np.ndarray, want: np.ndarray, what: str = ""):
