@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--diags", type=int, default=256, help="number of diagonals (256 = the benchmark workload)")
     ap.add_argument("--level", type=int, default=24, help="ciphertext level (24 = the benchmark workload)")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batched", "uneven", "serving", "paper-a", "paper-b"],
+                    choices=["single", "batched", "uneven", "serving", "paper-a", "paper-b", "cts", "stc"],
                     help="single: one LT per step (the headline); batched: 64 ciphertexts at levels "
                          "{8,16,24} and one shared 256-diagonal matrix per step; serving: Poisson "
                          "arrivals of LT requests through the continuous-batching server")
@@ -163,11 +163,14 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- byte model
-def algorithmic_bytes(cls: str, split, level: int, k: int, beta: int, n_diag: int, N: int) -> tuple:
+def algorithmic_bytes(cls: str, split, level: int, k: int, beta: int, n_diag: int, N: int,
+                      outer_rotated: int | None = None) -> tuple:
     """(bytes, launches) per LT of one kernel class in the TH/DH schedule:
     the words the step must read and write once (keys, diagonals, digits,
-    inputs, outputs), 8 bytes each."""
+    inputs, outputs), 8 bytes each.  outer_rotated: how many outer amounts are
+    nonzero (n3 - 1 for consecutive offsets from 0; up to n3 with a base)."""
     n1, n2, n3 = split
+    n_out = n3 - 1 if outer_rotated is None else outer_rotated
     ext = level + k
     limb = 8 * N
     if cls == "diag_mac":
@@ -179,8 +182,8 @@ def algorithmic_bytes(cls: str, split, level: int, k: int, beta: int, n_diag: in
         return limbs * limb, 1
     if cls == "ks_inner":
         p1 = (n1 - 1) * (beta * ext + 2 * beta * ext + level + 2 * ext)
-        p5 = (n3 - 1) * (beta * ext + 2 * beta * ext + ext + 4 * ext)
-        return (p1 + p5) * limb, (n1 - 1) + (n3 - 1)
+        p5 = n_out * (beta * ext + 2 * beta * ext + ext + 4 * ext)
+        return (p1 + p5) * limb, (n1 - 1) + n_out
     return None, None
 
 
@@ -688,6 +691,189 @@ def run_paper_shape(args, dist: Dist):
     }
 
 
+def chain_shapes(kind: str, log_slots: int, radices) -> list:
+    """(offset0, stride, D) of each stage of a factored slot DFT, first applied
+    first.  A group of r butterfly stages S_t .. S_{t+r-1} has its diagonals at
+    the multiples of 2^(t-1) from -(2^r - 1) 2^(t-1) to +(2^r - 1) 2^(t-1),
+    2^(r+1) - 1 of them, padded to 2^(r+1); the group that ends at the last
+    stage covers every multiple, 2^r from offset 0.  SlotToCoeff applies the
+    groups from S_1 up, CoeffToSlot (the inverses) from the last stage down."""
+    out, t = [], 1
+    for r in radices:
+        h = 1 << (t - 1)
+        if t + r - 1 == log_slots:
+            out.append((0, h, 1 << r))
+        else:
+            out.append((-((1 << r) - 1) * h, h, 1 << (r + 1)))
+        t += r
+    if t - 1 != log_slots:
+        raise ValueError("radices must sum to log2(N/2)")
+    return out if kind == "stc" else out[::-1]
+
+
+def run_chain(args, dist: Dist):
+    """One CoeffToSlot (or SlotToCoeff) transform per step: a chain of three
+    LTs (radices 5, 5, 5) from level 24 to 21 at N = 2^16, through
+    lt_eval_chain, each stage with its autotuned TH-BSGS split."""
+    import numpy as np
+    import torch
+    from paper_2605_17222_gb300 import binding, synth
+    kind = args.workload
+    device = f"cuda:{dist.local}"
+    torch.cuda.set_device(dist.local)
+    ps = synth.param_set(PARAMS)
+    g = binding.Context.from_params(ps, device=dist.local)
+    N, lvl0 = ps.n, LEVEL
+    radices = (5, 5, 5)
+    shapes = chain_shapes(kind, ps.log_n - 1, radices)
+    top = list(ps.q) + list(ps.p)
+    fs, cands = [], []
+    for i, (off0, stride, Dn) in enumerate(shapes):
+        t = synth.uniform_mod_device(SEED + 100 * i, f"chain/diag/{i}", top, N, count=Dn, device=device)
+        fs.append(g.upload_diagonals_device(t, stride=stride, level=ps.L, offset0=off0))
+        del t
+        cands.append(g.candidate_splits("th", lvl0 - i, Dn, 4))
+    keys_t = {}
+    for i, (off0, stride, Dn) in enumerate(shapes):
+        for sp in cands[i]:
+            for r in g.required_rotations("th", sp, Dn, stride, offset0=off0):
+                if r not in keys_t:
+                    keys_t[r] = synth.uniform_mod_device(SEED, f"key/{r}", ps.moduli, N, count=2 * g.beta_max,
+                                                         device=device)
+                    g.upload_rotation_key_device(r, keys_t[r])
+    splits = []
+    for i, f in enumerate(fs):
+        sample = g.ct_wrap(synth.uniform_mod_device(SEED + i, "chain/sample", list(ps.q[:lvl0 - i]), N, count=2,
+                                                    device=device), lvl0 - i)
+        sp, _ = g.autotune("th", sample, f, len(cands[i]))
+        splits.append(sp)
+    ct_t = synth.uniform_mod_device(SEED, "chain/ct", list(ps.q[:lvl0]), N, count=2, device=device)
+    ct = g.ct_wrap(ct_t, lvl0)
+    nst = len(shapes)
+    out = g.ct_empty(lvl0 - nst)
+    keep_host = not args.no_cpu_baseline and dist.rank == 0 and dist.world == 1
+    used = set()
+    for (off0, stride, Dn), sp in zip(shapes, splits):
+        used |= set(g.required_rotations("th", sp, Dn, stride, offset0=off0))
+    keys_t = {r: t for r, t in keys_t.items() if r in used} if keep_host else {}
+    torch.cuda.empty_cache()
+    stream = torch.cuda.current_stream()
+    for c in binding.KERNEL_CLASSES:
+        binding.profile_enable(c, True)
+    binding.profile_reset()
+    for _ in range(max(3, args.warmup)):
+        g.lt_eval_chain(ct, fs, out=out)
+    torch.cuda.synchronize()
+    shares = {c: binding.profile_read(c) for c in binding.KERNEL_CLASSES}
+    for c in binding.KERNEL_CLASSES:
+        binding.profile_enable(c, False)
+    tot = sum(v[0] for v in shares.values()) or 1.0
+    dominant = max(("diag_mac", "ks_inner"), key=lambda c: shares[c][0])
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    time.sleep(0.3)
+    binding.profile_reset()
+    binding.profile_enable(dominant, True)
+    l0 = binding.kernel_launches()
+    steps = max(1, args.steps)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i in range(steps):
+        g.lt_eval_chain(ct, fs, out=out)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    launches = binding.kernel_launches() - l0
+    dom_ms, dom_n = binding.profile_read(dominant)
+    binding.profile_enable(dominant, False)
+    step_ms = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(steps))
+    total_ms = dist.max(evs[0].elapsed_time(evs[-1]))
+    # end to end through the C ABI: host ciphertext in, host result out, every step
+    n_in, n_out = 2 * lvl0 * N, 2 * (lvl0 - nst) * N
+    h_in = torch.empty(n_in, dtype=torch.int64, pin_memory=True)
+    h_in.copy_(ct_t.reshape(-1).cpu())
+    h_out = torch.empty(n_out, dtype=torch.int64, pin_memory=True)
+    hin, hout = h_in.numpy().view(np.uint64), h_out.numpy().view(np.uint64)
+    d_in, d_out = g.ct_create(lvl0), g.ct_create(lvl0 - nst)
+    for _ in range(2):
+        g.h2d_async(d_in, hin)
+        g.lt_eval_chain(d_in, fs, out=d_out)
+        g.d2h_async(d_out, hout)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, steps // 2)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        g.h2d_async(d_in, hin)
+        g.lt_eval_chain(d_in, fs, out=d_out)
+        g.d2h_async(d_out, hout)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e2e_ms = dist.max(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    # roofline of the dominant kernel: its algorithmic bytes summed over the stages
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    per_chain, per_chain_launches = 0, 0
+    for i, ((off0, stride, Dn), sp) in enumerate(zip(shapes, splits)):
+        amounts = [(off0 + stride * sp[0] * sp[1] * kk) % (N // 2) for kk in range(sp[2])]
+        b, n = algorithmic_bytes(dominant, sp, lvl0 - i, ps.k, g.beta(lvl0 - i), Dn, N,
+                                 outer_rotated=sum(1 for a in amounts if a))
+        per_chain += b
+        per_chain_launches += n
+    ach = per_chain * steps / (dom_ms / 1e3) / 1e9 if dom_ms else None
+    unit = "CoeffToSlot/s" if kind == "cts" else "SlotToCoeff/s"
+    res = {
+        "metric": f"{'CoeffToSlot' if kind == 'cts' else 'SlotToCoeff'} transforms/s at N=2^16 (3 levels, "
+                  f"bit-exact TH-BSGS chain)",
+        "value": round(dist.world * steps / (total_ms / 1e3), 3), "unit": unit, "n_gpus": dist.world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(total_ms / steps, 4),
+        "p50_ms": round(step_ms[len(step_ms) // 2], 4), "p99_ms": round(step_ms[-1], 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (uniform residues drawn on the device; seeded)",
+        "config": {"workload": f"{kind}: factored slot DFT at N=2^16, level {lvl0} -> {lvl0 - nst}, radices "
+                               f"{list(radices)}, stages (offset0, stride, D) {shapes}",
+                   "splits": [list(s) for s in splits], "parallelism": f"replicas x{dist.world}",
+                   "l2": "diagonals + keys resident, several GB per step > L2; no flush"},
+        "lt_per_s": round(dist.world * steps * nst / (total_ms / 1e3), 3),
+        "roofline": {"kernel": dominant, "bound": "hbm", "achieved": round(ach, 1) if ach else None, "peak": peak,
+                     "unit": "GB/s", "frac": round(ach / peak, 4) if ach else None, "traffic": None,
+                     "algorithmic_bytes_per_chain": int(per_chain),
+                     "avg_launch_ms": round(dom_ms / dom_n, 4) if dom_n else None,
+                     "peak_source": "measured HBM copy bandwidth" if "hbm_gbs" in peaks else "fallback"},
+        "kernel_shares": {c: round(v[0] / tot, 4) for c, v in shares.items()},
+        "e2e": {"value": round(dist.world * e2e_steps / (e2e_ms / 1e3), 3), "unit": unit,
+                "h2d_bytes_per_step": n_in * 8, "d2h_bytes_per_step": n_out * 8,
+                "ms_per_step": round(e2e_ms / e2e_steps, 4)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if keep_host:
+        t0 = time.perf_counter()
+        from oracle import lt as olt
+        from oracle.ckks import Ctx
+        keys = {r: binding.to_host(t).reshape(g.beta_max, 2, ps.L + ps.k, N) for r, t in keys_t.items()}
+        stages = []
+        for i, ((off0, stride, Dn), sp) in enumerate(zip(shapes, splits)):
+            dt = synth.uniform_mod_device(SEED + 100 * i, f"chain/diag/{i}", top, N, count=Dn, device=device)
+            stages.append((np.ascontiguousarray(binding.to_host(dt)), "th", sp, stride, off0))
+            del dt
+        cth = binding.to_host(ct_t)
+        octx = Ctx(ps)
+        t1 = time.perf_counter()
+        olt.lt_chain(octx, (np.ascontiguousarray(cth[0]), np.ascontiguousarray(cth[1])), stages, keys)
+        cpu_s = time.perf_counter() - t1
+        res["cpu_baseline"] = {"value": round(1.0 / cpu_s, 5), "unit": unit, "cores": cores_used(), "kind": "oracle",
+                               "sample": f"one full oracle chain ({nst} LTs) of the workload, "
+                                         f"{cpu_s:.1f} s (setup {t1 - t0:.1f} s untimed)"}
+    return res
+
+
 def run_serving(args, dist: Dist):
     """Poisson arrivals (rate, duration; seed 4) of single-LT requests, each with
     N from {2^15, 2^16}, 32..512 diagonals (powers of two) and a level of
@@ -838,6 +1024,8 @@ def main():
             res = run_uneven(args, dist)
         elif args.workload in PAPER_SHAPES:
             res = run_paper_shape(args, dist)
+        elif args.workload in ("cts", "stc"):
+            res = run_chain(args, dist)
         else:
             res = run_ours(args, dist)
         if dist.rank == 0 and res is not None:
