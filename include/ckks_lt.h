@@ -237,7 +237,8 @@ ckks_status lt_choose_split(ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_
  * and are exported for step-by-step checking and custom schedules. */
 
 /* Forward (inverse = 0) or inverse (inverse = 1) negacyclic NTT, in place, of
- * a polynomial at `level` with (ext = 1) or without (ext = 0) the P limbs. */
+ * a polynomial at `level` with (ext = 1) or without (ext = 0) the P limbs.
+ * Words must be canonical residues (limb j in [0, q_j)); so are the results. */
 ckks_status ckks_poly_ntt(ckks_ctx* ctx, uint64_t* poly, uint32_t level, int ext, int inverse, void* stream);
 
 /* Decompose (ModUp), Fig. 1 and Eq. (3): digits of phi_rot(c) (rot = 0: of c)

@@ -170,6 +170,49 @@ __device__ __forceinline__ u64 canon4(u64 x, u64 q) {
     return x >= q ? x - q : x;
 }
 
+// Any 64-bit word -> [0, 2q): the Shoup product by 1 (floor(2^64 / q) = mu_hi).
+__device__ __forceinline__ u64 red2(u64 x, u64 q, u64 mu_hi) { return x - __umul64hi(x, mu_hi) * q; }
+
+// ------------------------------------------------------------------ growing butterflies
+// For moduli well below 2^64 the per-butterfly conditional subtraction that
+// keeps a lazy word bounded can be dropped inside a pass:
+//   CT: if both inputs are below B, (a + v, a - v + 2q) with v = b w mod q in
+//       [0, 2q) are both below B + 2q.  The 2 log N <= 32 stages of a forward
+//       transform from [0, q) stay below 33q, below 2^64 for q < 2^58.
+//   GS: if both inputs are below M (a multiple of q), (a + b, (a - b + M) w
+//       mod q) are below 2M.  The <= 8 stages of one pass from [0, B) stay
+//       below 2^8 B; a pass starts from [0, q) (row) or [0, 2q) (column), so
+//       everything stays below 2^9 q < 2^64 for q < 2^55.
+// Wider moduli (the 60-bit special primes) take the reducing butterflies.
+constexpr u64 FWD_GROW_MAX = 1ull << 58;
+constexpr u64 INV_GROW_MAX = 1ull << 55;
+
+template <bool GROW>
+__device__ __forceinline__ void ct(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
+    if constexpr (GROW) {
+        u64 w, ws;
+        tw_at(tab, idx, w, ws);
+        const u64 v = mul_shoup_lazy(b, w, ws, q);
+        b = a - v + 2 * q;
+        a = a + v;
+    } else {
+        ct_bfly(a, b, tab, idx, q);
+    }
+}
+
+template <bool GROW>
+__device__ __forceinline__ void gs(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q, u64 M) {
+    if constexpr (GROW) {
+        u64 w, ws;
+        tw_at(tab, idx, w, ws);
+        const u64 s = a + b;
+        b = mul_shoup_lazy(a - b + M, w, ws, q);
+        a = s;
+    } else {
+        gs_bfly(a, b, tab, idx, q);
+    }
+}
+
 // Every pass works on "lines" of S = 2^LOGS words (a column of the R x C
 // view in the column pass, a row in the row pass) with 16 words per thread
 // and TPL = S/16 threads per line, in two layouts:
@@ -185,6 +228,30 @@ __device__ __forceinline__ u32 pad16(u32 i) { return i + (i >> 4); }
 
 // ------------------------------------------------------------------ forward, column pass
 // Global stages 0..LOGS-1 (m = 2^ss, twiddle psi^brv(m + r / 2t_r)).
+template <int LOGS, bool GROW>
+__device__ __forceinline__ void fwd_cols_stages(u64 (&x)[16], u64* sm, u32 u, u32 c, const ulonglong2* tw, u64 q) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
+#pragma unroll
+    for (int ss = 0; ss < 4; ss++) {
+        const int tv = 8 >> ss;
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & tv)) ct<GROW>(x[v], x[v + tv], tw, (1u << ss) + (v >> (4 - ss)), q);
+    }
+#pragma unroll
+    for (int v = 0; v < 16; v++) sm[(u + TPL * v) * W + c] = x[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = sm[(16 * u + v) * W + c];
+#pragma unroll
+    for (int ss = 4; ss < LOGS; ss++) {
+        const int t = S >> (ss + 1);
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & t)) ct<GROW>(x[v], x[v + t], tw, (1u << ss) + ((16 * u + v) >> (LOGS - ss)), q);
+    }
+}
+
 template <int LOGS, bool BCONV>
 __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<FwdJob> jobs) {
@@ -216,54 +283,26 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
 #pragma unroll
         for (int v = 0; v < 16; v++) x[v] = J.src[(size_t)(u + TPL * v) * C + col];
     }
-#pragma unroll
-    for (int ss = 0; ss < 4; ss++) {
-        const int tv = 8 >> ss;
-#pragma unroll
-        for (int v = 0; v < 16; v++)
-            if (!(v & tv)) ct_bfly(x[v], x[v + tv], tw, (1u << ss) + (v >> (4 - ss)), q);
-    }
-#pragma unroll
-    for (int v = 0; v < 16; v++) sm[(u + TPL * v) * W + c] = x[v];
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < 16; v++) x[v] = sm[(16 * u + v) * W + c];
-#pragma unroll
-    for (int ss = 4; ss < LOGS; ss++) {
-        const int t = S >> (ss + 1);
-#pragma unroll
-        for (int v = 0; v < 16; v++)
-            if (!(v & t)) ct_bfly(x[v], x[v + t], tw, (1u << ss) + ((16 * u + v) >> (LOGS - ss)), q);
-    }
+    // words enter in [0, q); they leave below 4q (reducing) or 17q (growing)
+    if (q < FWD_GROW_MAX) fwd_cols_stages<LOGS, true>(x, sm, u, c, tw, q);
+    else fwd_cols_stages<LOGS, false>(x, sm, u, c, tw, q);
 #pragma unroll
     for (int v = 0; v < 16; v++) J.dst[(size_t)(16 * u + v) * C + col] = x[v];
 }
 
 // ------------------------------------------------------------------ forward, row pass
 // Global stages log_r..log_n-1 (m = 2^(log_r+ss), twiddle psi^brv(m + row 2^ss + x / 2t)).
-template <int LOGS, bool SUBMUL>
-__global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__ NttTables T,
-                                                      const __grid_constant__ Jobs<FwdJob> jobs) {
-    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
-    __shared__ u64 sm[B * SP];
-    const u32 log_n = T.log_n, N = 1u << log_n, log_r = log_n - LOGS;
-    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
-    const u32 row = blockIdx.x * B + rl;
-    const FwdJob& J = jobs.j[blockIdx.y];
-    const u64 q = T.mods[J.mod].q;
-    const ulonglong2* tw = T.psi + (size_t)J.mod * N;
-    const size_t base = (size_t)row * S;
-    u64* sr = sm + rl * SP;
-    u64 x[16];
-#pragma unroll
-    for (int v = 0; v < 16; v++) x[v] = J.dst[base + u + TPL * v];
+template <int LOGS, bool GROW>
+__device__ __forceinline__ void fwd_rows_stages(u64 (&x)[16], u64* sr, u32 u, u32 row, u32 log_r,
+                                                const ulonglong2* tw, u64 q) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16;
 #pragma unroll
     for (int ss = 0; ss < 4; ss++) {
         const int tv = 8 >> ss;
         const u32 b0 = (1u << (log_r + ss)) + (row << ss);
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & tv)) ct_bfly(x[v], x[v + tv], tw, b0 + (v >> (4 - ss)), q);
+            if (!(v & tv)) ct<GROW>(x[v], x[v + tv], tw, b0 + (v >> (4 - ss)), q);
     }
 #pragma unroll
     for (int v = 0; v < 16; v++) sr[pad16(u + TPL * v)] = x[v];
@@ -276,8 +315,30 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__
         const u32 b0 = (1u << (log_r + ss)) + (row << ss);
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & t)) ct_bfly(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (LOGS - ss)), q);
+            if (!(v & t)) ct<GROW>(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (LOGS - ss)), q);
     }
+}
+
+template <int LOGS, bool SUBMUL>
+__global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__ NttTables T,
+                                                      const __grid_constant__ Jobs<FwdJob> jobs) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
+    __shared__ u64 sm[B * SP];
+    const u32 log_n = T.log_n, N = 1u << log_n, log_r = log_n - LOGS;
+    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
+    const u32 row = blockIdx.x * B + rl;
+    const FwdJob& J = jobs.j[blockIdx.y];
+    const ModC m = T.mods[J.mod];
+    const u64 q = m.q;
+    const ulonglong2* tw = T.psi + (size_t)J.mod * N;
+    const size_t base = (size_t)row * S;
+    u64* sr = sm + rl * SP;
+    u64 x[16];
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = J.dst[base + u + TPL * v];
+    const bool grow = q < FWD_GROW_MAX;
+    if (grow) fwd_rows_stages<LOGS, true>(x, sr, u, row, log_r, tw, q);
+    else fwd_rows_stages<LOGS, false>(x, sr, u, row, log_r, tw, q);
     __syncwarp();
 #pragma unroll
     for (int v = 0; v < 16; v++) sr[pad16(16 * u + v)] = x[v];
@@ -285,7 +346,14 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__
 #pragma unroll
     for (int v = 0; v < 16; v++) {
         const u32 xi = u + TPL * v;
-        const u64 val = canon4(sr[pad16(xi)], q);
+        const u64 y = sr[pad16(xi)];
+        u64 val;
+        if (grow) {  // below 33q
+            val = red2(y, q, m.mu_hi);
+            val = val >= q ? val - q : val;
+        } else {  // below 4q
+            val = canon4(y, q);
+        }
         if constexpr (SUBMUL) {
             J.subout[base + xi] = mul_shoup(sub_mod(J.subx[base + xi], val, q), J.c, J.c_sh, q);
         } else {
@@ -296,6 +364,37 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__
 
 // ------------------------------------------------------------------ inverse, row pass
 // GS stages with half-width t = 1..S/2 (m = N/2t, twiddle psi^-brv(m + row S/2t + x/2t)).
+// Growing form: words enter below q; the i-th stage of the pass takes M = q 2^i.
+template <int LOGS, bool GROW>
+__device__ __forceinline__ void inv_rows_stages(u64 (&x)[16], u64* sr, u32 u, u32 row, u32 N,
+                                                const ulonglong2* tw, u64 q) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16;
+#pragma unroll
+    for (int lt = 0; lt < LOGS - 4; lt++) {  // t = 1 .. TPL/2
+        const int t = 1 << lt;
+        const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
+        const u64 M = q << lt;
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & t)) gs<GROW>(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (lt + 1)), q, M);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < 16; v++) sr[pad16(16 * u + v)] = x[v];
+    __syncwarp();
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = sr[pad16(u + TPL * v)];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {  // t = TPL * 2^k
+        const int lt = (LOGS - 4) + k;
+        const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
+        const u64 M = q << lt;
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & (1 << k))) gs<GROW>(x[v], x[v + (1 << k)], tw, b0 + (v >> (k + 1)), q, M);
+    }
+}
+
 template <int LOGS, bool GATHER>
 __global__ void __launch_bounds__(THREADS, 4) k_inv_rows(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<InvJob> jobs) {
@@ -305,7 +404,8 @@ __global__ void __launch_bounds__(THREADS, 4) k_inv_rows(const __grid_constant__
     const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
     const u32 row = blockIdx.x * B + rl;
     const InvJob& J = jobs.j[blockIdx.y];
-    const u64 q = T.mods[J.mod].q;
+    const ModC m = T.mods[J.mod];
+    const u64 q = m.q;
     const ulonglong2* tw = T.ipsi + (size_t)J.mod * N;
     const size_t base = (size_t)row * S;
     u64* sr = sm + rl * SP;
@@ -321,27 +421,12 @@ __global__ void __launch_bounds__(THREADS, 4) k_inv_rows(const __grid_constant__
     __syncwarp();
 #pragma unroll
     for (int v = 0; v < 16; v++) x[v] = sr[pad16(16 * u + v)];
+    if (q < INV_GROW_MAX) {
+        inv_rows_stages<LOGS, true>(x, sr, u, row, N, tw, q);
 #pragma unroll
-    for (int lt = 0; lt < LOGS - 4; lt++) {  // t = 1 .. TPL/2
-        const int t = 1 << lt;
-        const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
-#pragma unroll
-        for (int v = 0; v < 16; v++)
-            if (!(v & t)) gs_bfly(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (lt + 1)), q);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int v = 0; v < 16; v++) sr[pad16(16 * u + v)] = x[v];
-    __syncwarp();
-#pragma unroll
-    for (int v = 0; v < 16; v++) x[v] = sr[pad16(u + TPL * v)];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {  // t = TPL * 2^k
-        const int lt = (LOGS - 4) + k;
-        const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
-#pragma unroll
-        for (int v = 0; v < 16; v++)
-            if (!(v & (1 << k))) gs_bfly(x[v], x[v + (1 << k)], tw, b0 + (v >> (k + 1)), q);
+        for (int v = 0; v < 16; v++) x[v] = red2(x[v], q, m.mu_hi);  // below 2^8 q -> [0, 2q)
+    } else {
+        inv_rows_stages<LOGS, false>(x, sr, u, row, N, tw, q);  // stays in [0, 2q)
     }
 #pragma unroll
     for (int v = 0; v < 16; v++) J.tmp[base + u + TPL * v] = x[v];
@@ -350,6 +435,33 @@ __global__ void __launch_bounds__(THREADS, 4) k_inv_rows(const __grid_constant__
 // ------------------------------------------------------------------ inverse, column pass
 // GS stages with half-width C*t_r, t_r = 1..S/2 (m = S/2t_r, twiddle psi^-brv(m + r/2t_r)),
 // then the scaling by c (N^-1 and any per-limb constant).
+// Growing form: words enter below 2q; the i-th stage of the pass takes M = 2q 2^i.
+template <int LOGS, bool GROW>
+__device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u32 c, const ulonglong2* tw, u64 q) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
+#pragma unroll
+    for (int lt = 0; lt < LOGS - 4; lt++) {
+        const int t = 1 << lt;
+        const u64 M = (2 * q) << lt;
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & t)) gs<GROW>(x[v], x[v + t], tw, (S >> (lt + 1)) + ((16 * u + v) >> (lt + 1)), q, M);
+    }
+#pragma unroll
+    for (int v = 0; v < 16; v++) sm[(16 * u + v) * W + c] = x[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = sm[(u + TPL * v) * W + c];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int lt = (LOGS - 4) + k;
+        const u64 M = (2 * q) << lt;
+#pragma unroll
+        for (int v = 0; v < 16; v++)
+            if (!(v & (1 << k))) gs<GROW>(x[v], x[v + (1 << k)], tw, (S >> (lt + 1)) + (v >> (k + 1)), q, M);
+    }
+}
+
 template <int LOGS>
 __global__ void __launch_bounds__(THREADS, 4) k_inv_cols(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<InvJob> jobs) {
@@ -364,25 +476,9 @@ __global__ void __launch_bounds__(THREADS, 4) k_inv_cols(const __grid_constant__
     u64 x[16];
 #pragma unroll
     for (int v = 0; v < 16; v++) x[v] = J.tmp[(size_t)(16 * u + v) * C + col];
-#pragma unroll
-    for (int lt = 0; lt < LOGS - 4; lt++) {
-        const int t = 1 << lt;
-#pragma unroll
-        for (int v = 0; v < 16; v++)
-            if (!(v & t)) gs_bfly(x[v], x[v + t], tw, (S >> (lt + 1)) + ((16 * u + v) >> (lt + 1)), q);
-    }
-#pragma unroll
-    for (int v = 0; v < 16; v++) sm[(16 * u + v) * W + c] = x[v];
-    __syncthreads();
-#pragma unroll
-    for (int v = 0; v < 16; v++) x[v] = sm[(u + TPL * v) * W + c];
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int lt = (LOGS - 4) + k;
-#pragma unroll
-        for (int v = 0; v < 16; v++)
-            if (!(v & (1 << k))) gs_bfly(x[v], x[v + (1 << k)], tw, (S >> (lt + 1)) + (v >> (k + 1)), q);
-    }
+    if (q < INV_GROW_MAX) inv_cols_stages<LOGS, true>(x, sm, u, c, tw, q);
+    else inv_cols_stages<LOGS, false>(x, sm, u, c, tw, q);
+    // mul_shoup reduces any 64-bit word fully
 #pragma unroll
     for (int v = 0; v < 16; v++) J.dst[(size_t)(u + TPL * v) * C + col] = mul_shoup(x[v], J.c, J.c_sh, q);
 }
