@@ -350,14 +350,19 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
     // Runs, in order: k_count diagonal runs; at j = 0 the A and B runs; at j > 0
     // the beta digit runs and the A run.  A and B are skipped for the lifted
     // ciphertext on P limbs (zero words).
+    // source run of the middle-layer gather for every j (Eq. 8 maps an aligned
+    // run onto one aligned run), computed once by the whole CTA
+    u32* srun_of = (u32*)(smem + (size_t)NS * stage_runs * RUN);
+    for (u32 jj = l; jj < n2; jj += RUN) srun_of[jj] = jj ? auto_src(run * RUN, a.gal_mid[jj], a.log_n) / RUN : run;
+
     auto issue = [&](u32 it) {
         if (it >= n1n2) return;
-        const u32 j = it / n1, i = it % n1;
+        const u32 j = n1 == 1 ? it : it / n1, i = n1 == 1 ? 0u : it % n1;
         u64* st = smem + (size_t)(it % NS) * stage_runs * RUN;
         u64* bar = &full_bar[it % NS];
         const bool lifted = (i == 0) && a.lift0;
         const bool copy_a = !lifted || lift_limb;
-        const u32 srun = j ? auto_src(run * RUN, a.gal_mid[j], a.log_n) / RUN : run;
+        const u32 srun = srun_of[j];
         const u32 n_ab = j == 0 ? (copy_a ? 2u : 0u) : (copy_a ? 1u : 0u);
         const u32 n_dig = j == 0 ? 0u : beta;
         mbar_expect_tx(bar, (k_count + n_dig + n_ab) * RB);
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
     u32 pm = 0;          // in-run source position of the middle-layer gather of the current j
 
     for (u32 it = 0; it < n1n2; it++) {
-        const u32 j = it / n1, i = it % n1;
+        const u32 j = n1 == 1 ? it : it / n1, i = n1 == 1 ? 0u : it % n1;
         if (j > 0 && i == 0) {
             // a new giant index: its key words (not gathered) come straight from
             // global memory; the loads overlap the wait for the stage below
@@ -503,7 +508,7 @@ constexpr size_t DM_SMEM_MAX = 226 * 1024;  // dynamic part; the mbarriers take 
 template <int K3, int RUN, int NS, int KB>
 bool try_staged(const DiagMacArgs& a, cudaStream_t st) {
     const size_t beta = a.n2 > 1 ? a.beta : 0;
-    const size_t sm = 8ull * RUN * NS * (K3 + beta + 2);
+    const size_t sm = 8ull * RUN * NS * (K3 + beta + 2) + ((4ull * a.n2 + 15) & ~15ull);  // stages + srun table
     const u32 N = 1u << a.log_n;
     if (sm > DM_SMEM_MAX || N % RUN || beta > (size_t)KB) return false;
     static int attr_ok = -1;
