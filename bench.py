@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--diags", type=int, default=256, help="number of diagonals (256 = the benchmark workload)")
     ap.add_argument("--level", type=int, default=24, help="ciphertext level (24 = the benchmark workload)")
     ap.add_argument("--workload", default="single",
-                    choices=["single", "batched", "uneven", "serving", "paper-a", "paper-b", "cts", "stc"],
+                    choices=["single", "batched", "uneven", "serving", "paper-a", "paper-b", "cts", "stc", "steps"],
                     help="single: one LT per step (the headline); batched: 64 ciphertexts at levels "
                          "{8,16,24} and one shared 256-diagonal matrix per step; serving: Poisson "
                          "arrivals of LT requests through the continuous-batching server")
@@ -874,6 +874,53 @@ def run_chain(args, dist: Dist):
     return res
 
 
+def run_steps(args, dist: Dist):
+    """The key-switching steps on their own at N = 2^16, level 24 (no LT):
+    Decompose of a ciphertext's c1 (144 limbs of forward NTT with the basis
+    conversion fused into the column pass, 24 limbs of inverse NTT) and the
+    forward NTT of a 28-limb extended polynomial, each timed over `steps`
+    calls with CUDA events, with the library's per-class kernel times.  The
+    device holds a few hundred MB, which keeps ncu captures of the NTT
+    passes small."""
+    import torch
+    from paper_2605_17222_gb300 import binding, synth
+    device = f"cuda:{dist.local}"
+    torch.cuda.set_device(dist.local)
+    ps = synth.param_set(PARAMS)
+    g = binding.Context.from_params(ps, device=dist.local)
+    N, L, K = ps.n, LEVEL, ps.k
+    cs = synth.uniform_mod_device(SEED, "steps/c", list(ps.q[:L]), N, count=8, device=device)
+    digs = [torch.empty((g.beta(L), L + K, N), dtype=torch.int64, device=device) for _ in range(8)]
+    ext = synth.uniform_mod_device(SEED, "steps/ext", list(ps.q[:L]) + list(ps.p), N, count=8, device=device)
+    steps = max(1, args.steps)
+    for i in range(max(3, args.warmup)):
+        g.decompose(cs[i % 8], L, digits=digs[i % 8])
+        g.ntt(ext[i % 8], L, True, False)
+    torch.cuda.synchronize()
+    res = {"metric": "key-switching steps at N=2^16, level 24 (us per call)", "unit": "us", "steps": steps,
+           "warmup": args.warmup, "n_gpus": 1, "higher_is_better": False, "dtype": "u64",
+           "data": "synthetic (uniform residues drawn on the device; seeded)",
+           "config": {"workload": "steps: Decompose of c1 at level 24 (alpha 4, beta 6, k 4), forward NTT of a "
+                                  "28-limb extended polynomial"}}
+    for name, fn in [("decompose", lambda i: g.decompose(cs[i % 8], L, digits=digs[i % 8])),
+                     ("ntt_fwd_ext", lambda i: g.ntt(ext[i % 8], L, True, False))]:
+        for c in binding.KERNEL_CLASSES:
+            binding.profile_enable(c, True)
+        binding.profile_reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(steps):
+            fn(i)
+        e1.record()
+        torch.cuda.synchronize()
+        per = {c: binding.profile_read(c) for c in binding.KERNEL_CLASSES}
+        for c in binding.KERNEL_CLASSES:
+            binding.profile_enable(c, False)
+        res[name] = {"us_per_call": round(e0.elapsed_time(e1) * 1e3 / steps, 2),
+                     "kernels_us_per_call": {c: round(ms * 1e3 / steps, 2) for c, (ms, n) in per.items() if n}}
+    return res
+
+
 def run_serving(args, dist: Dist):
     """Poisson arrivals (rate, duration; seed 4) of single-LT requests, each with
     N from {2^15, 2^16}, 32..512 diagonals (powers of two) and a level of
@@ -1026,6 +1073,8 @@ def main():
             res = run_paper_shape(args, dist)
         elif args.workload in ("cts", "stc"):
             res = run_chain(args, dist)
+        elif args.workload == "steps":
+            res = run_steps(args, dist)
         else:
             res = run_ours(args, dist)
         if dist.rank == 0 and res is not None:
