@@ -626,6 +626,16 @@ PAPER_SHAPES = {
 }
 
 
+def fpga_offchip(params: str) -> dict:
+    """The paper's data-path off-chip model at its own knobs (Sec. IV formulas),
+    next to the total its resource table prints; units of 2^30 bytes, 54-bit words."""
+    from paper_2605_17222_gb300 import memory_model as mm
+    shape, knobs, printed = mm.PAPER_SETS[{"setA": "Set-A", "setB": "Set-B"}[params]]
+    by = mm.offchip_by_category(shape, knobs)
+    return {"model": round(mm.paper_units(sum(by.values())), 3), "printed": printed, "unit": "2^30 bytes (54-bit words)",
+            "by_category": {c: round(mm.paper_units(v), 3) for c, v in by.items()}}
+
+
 def run_paper_shape(args, dist: Dist):
     """One dense LT (n = N/2 nonzero diagonals) with the paper's parameter set
     and split, timed like the headline workload."""
@@ -686,6 +696,7 @@ def run_paper_shape(args, dist: Dist):
                                f"alpha={ps.alpha}, beta={g.beta(lvl)}, n={Dn}, split {split}",
                    "split": list(split)},
         "paper_fpga_ms_context": cfg["fpga_ms"],
+        "paper_fpga_offchip": fpga_offchip(cfg["params"]),
         "hbm_roofline_lt": {"compulsory_bytes": comp, "frac": round(comp / (ms / 1e3) / 1e9 / peak, 4)},
         "clocks": clk,
     }
