@@ -490,8 +490,11 @@ def run_batched(args, dist: Dist):
     g = binding.Context.from_params(ps, device=dist.local)
     n_ct = 64
     levels = [int(v) for v in np.random.default_rng(2).choice([8, 16, 24], n_ct)]
-    splits = {lv: g.choose_split("th", lv, D) for lv in sorted(set(levels))}
-    rots = sorted({r for lv, sp in splits.items() for r in g.required_rotations("th", sp, D, 1)})
+    lvs = sorted(set(levels))
+    # keys for the cost model's best candidates at every level; the library's
+    # autotuners then pick one split per level for single LTs and one for the batch
+    cands = {lv: g.candidate_splits("th", lv, D, 6) for lv in lvs}
+    rots = sorted({r for lv in lvs for sp in cands[lv] for r in g.required_rotations("th", sp, D, 1)})
     for r in rots:
         t = synth.uniform_mod_device(SEED, f"key/{r}", ps.moduli, ps.n, count=2 * g.beta_max, device=device)
         g.upload_rotation_key_device(r, t)
@@ -503,7 +506,10 @@ def run_batched(args, dist: Dist):
     cts = [g.ct_wrap(synth.uniform_mod_device(SEED + 1 + n, f"ct/{n}", list(ps.q[:lv]), ps.n, count=2,
                                               device=device), lv) for n, lv in enumerate(levels)]
     outs = [g.ct_empty(lv - 1) for lv in levels]
+    single = {lv: g.autotune("th", next(c for c in cts if c.level == lv), f, len(cands[lv]))[0] for lv in lvs}
+    splits = {lv: g.autotune_batch("th", [c for c in cts if c.level == lv], f, len(cands[lv]))[0] for lv in lvs}
     sp_list = [splits[lv] for lv in levels]
+    seq_list = [single[lv] for lv in levels]
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
 
@@ -522,7 +528,7 @@ def run_batched(args, dist: Dist):
         return dist.max(e0.elapsed_time(e1))
 
     def sequential():
-        for c, o, sp in zip(cts, outs, sp_list):
+        for c, o, sp in zip(cts, outs, seq_list):
             g.lt_eval(c, f, "th", sp, out=o)
 
     rec = g.lt_graph(cts, [f] * n_ct, algos=["th"] * n_ct, splits=sp_list, outs=outs)
@@ -555,6 +561,9 @@ def run_batched(args, dist: Dist):
                                f"{D}-diagonal matrix; one recorded lt_eval_batch per step",
                    "levels": {str(lv): levels.count(lv) for lv in sorted(set(levels))},
                    "splits": {str(lv): list(sp) for lv, sp in splits.items()},
+                   "split_choice": "per level: lt_autotune_batch over the level's ciphertexts (batch) and "
+                                   "lt_autotune on one of them (sequential), over the cost model's 6 best",
+                   "sequential_splits": {str(lv): list(sp) for lv, sp in single.items()},
                    "l2": "inputs larger than L2; no flush"},
         "batched_graph_lt_per_s": round(val, 3),
         "batched_call_lt_per_s": round(dist.world * n_ct * steps / (ms_batch / 1e3), 3),

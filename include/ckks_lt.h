@@ -227,6 +227,18 @@ int32_t lt_candidate_splits(const ckks_ctx* ctx, lt_algo algo, uint32_t level, u
 ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, const ckks_diags* f,
                         uint32_t max_candidates, lt_split* chosen, double* best_ms);
 
+/* Measuring autotuner for batches: the same candidates as lt_autotune, each
+ * timed as one lt_eval_batch over the `count` sample ciphertexts (one level,
+ * all multiplied by f) on a private stream, so that the choice reflects what a
+ * batch shares -- every key and diagonal word is read once for the group, which
+ * moves the cost from HBM towards the middle layer's multiply-accumulates.
+ * Returns the fastest split and its time per batch; records nothing (the
+ * single-LT choice for the shape is unchanged).  Synchronous; allocates
+ * `count` output ciphertexts for its own use.  EINVAL if the samples are not
+ * all at one level, ENOKEY if no candidate has all of its keys. */
+ckks_status lt_autotune_batch(ckks_ctx* ctx, lt_algo algo, uint32_t count, const ckks_ct* const* samples,
+                              const ckks_diags* f, uint32_t max_candidates, lt_split* chosen, double* best_ms);
+
 /* The split the library would choose for (algo, level, n_diag) with stride 1:
  * the autotuned one if lt_autotune has measured that shape, else the model's. */
 ckks_status lt_choose_split(ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out);

@@ -77,6 +77,7 @@ def lib():
         "lt_eval_chain": [P, P, U32, P, P, P, P, P, P],
         "lt_choose_split": [P, I, U32, U32, P],
         "lt_autotune": [P, I, P, P, U32, P, P],
+        "lt_autotune_batch": [P, I, U32, P, P, U32, P, P],
         "ckks_poly_ntt": [P, P, U32, I, I, P],
         "ckks_decompose": [P, U32, P, I32, P, P],
         "ckks_ks_inner": [P, U32, P, I32, I32, P, I, P, P, I, P],
@@ -301,6 +302,16 @@ class Context:
         sp, ms = Split(), ctypes.c_double()
         check(lib().lt_autotune(self.h, ALGOS[algo], sample.handle, diags.handle, max_candidates, ctypes.byref(sp),
                                 ctypes.byref(ms)))
+        return sp.tuple(), ms.value
+
+    def autotune_batch(self, algo: str, samples, diags: "Diagonals", max_candidates: int = 6):
+        """Time the model's best candidate splits as one lt_eval_batch over `samples`
+        (one level); returns (fastest split, ms per batch)."""
+        n = len(samples)
+        arr = (ctypes.c_void_p * n)(*[c.handle for c in samples])
+        sp, ms = Split(), ctypes.c_double()
+        check(lib().lt_autotune_batch(self.h, ALGOS[algo], n, arr, diags.handle, max_candidates, ctypes.byref(sp),
+                                      ctypes.byref(ms)))
         return sp.tuple(), ms.value
 
     def candidate_splits(self, algo: str, level: int, n_diag: int, count: int):

@@ -1363,6 +1363,67 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
     return rc;
 }
 
+ckks_status lt_autotune_batch(ckks_ctx* ctx, lt_algo algo, uint32_t count, const ckks_ct* const* samples,
+                              const ckks_diags* f, uint32_t max_candidates, lt_split* chosen, double* best_ms) {
+    cudaStream_t st = nullptr;
+    std::vector<ckks_ct*> outs;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ckks_status rc = guarded([&] {
+        if (!ctx || !samples || !f || !count) fail(CKKS_EINVAL, "null argument or empty batch");
+        const u32 level = samples[0] ? samples[0]->level : 0, D = f->n_diag;
+        for (u32 i = 0; i < count; i++)
+            if (!samples[i] || samples[i]->ctx != ctx || samples[i]->level != level)
+                fail(CKKS_EINVAL, "samples must be ciphertexts of this context at one level");
+        if (level < 2 || level > f->level) fail(CKKS_EINVAL, "bad sample level");
+        CK(cudaSetDevice(ctx->device));
+        std::vector<lt_split> cand;
+        for (const lt_split& sp : ranked_splits(ctx, algo, level, D)) {
+            bool ok = true;
+            for (int64_t r : rotations(ctx, algo, sp, f))
+                if (!ctx->keys.count(ctx->rotkey(r))) ok = false;
+            if (ok) cand.push_back(sp);
+            if (cand.size() >= std::max<u32>(1, max_candidates)) break;
+        }
+        if (cand.empty()) fail(CKKS_ENOKEY, "no candidate split has all of its rotation keys");
+        CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (u32 i = 0; i < count; i++)
+            outs.push_back(new ckks_ct{ctx, level - 1, ctx->dalloc(2ull * (level - 1) * ctx->N), true});
+        std::vector<const ckks_diags*> fs(count, f);
+        std::vector<lt_algo> al(count, algo);
+        double best = 1e300;
+        lt_split bsp = cand[0];
+        for (const lt_split& sp : cand) {
+            std::vector<lt_split> sps(count, sp);
+            auto run = [&] {
+                const ckks_status r = lt_eval_batch(ctx, count, samples, fs.data(), al.data(), sps.data(),
+                                                    outs.data(), st);
+                if (r != CKKS_OK) fail(r, "batch evaluation failed while tuning");
+            };
+            run();  // warm-up (tables, attributes)
+            CK(cudaEventRecord(e0, st));
+            const int reps = 2;
+            for (int r = 0; r < reps; r++) run();
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms / reps < best) best = ms / reps, bsp = sp;
+        }
+        if (chosen) *chosen = bsp;
+        if (best_ms) *best_ms = best;
+    });
+    for (ckks_ct* o : outs) {
+        ctx->dfree(o->d, 2ull * o->level * ctx->N);
+        delete o;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return rc;
+}
+
 ckks_status lt_choose_split(ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out) {
     return guarded([&] {
         if (!ctx || !out) fail(CKKS_EINVAL, "null argument");

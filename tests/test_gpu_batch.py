@@ -114,3 +114,27 @@ def test_toy_batch_two_matrices_with_strides():
         assert_same(outs[n].numpy(), single.numpy(), f"item {n}")
     want = np.stack(olt.lt_th_bsgs(pa.ctx, cts[0], pa.diags, pa.keys, 2, 2, 4, stride=4)[0])
     assert_same(outs[0].numpy(), want, "strided item vs oracle")
+
+
+def test_batch_autotuner_picks_a_candidate_and_stays_exact():
+    """lt_autotune_batch times the candidates as one batch and returns one of
+    them; the batch evaluated with it equals the oracle; mixed levels are refused."""
+    from paper_2605_17222_gb300 import binding
+    pb = make_problem("toy", 0, 64)
+    g = gpu_context("toy")
+    f = upload_problem(g, pb)
+    cands = g.candidate_splits("th", pb.level, 64, 3)
+    for sp in cands:
+        ensure_keys(pb, "th", sp)
+    upload_problem(g, pb)
+    cts, _ = _encrypt_many(pb, [4, 4, 4, 4], 500)
+    ins = [g.ct_from_host(np.stack(ct)) for ct in cts]
+    split, ms = g.autotune_batch("th", ins, f, len(cands))
+    assert split in cands and ms > 0
+    outs = g.lt_eval_batch(ins, [f] * 4, algos=["th"] * 4, splits=[split] * 4)
+    want = np.stack(olt.lt_th_bsgs(pb.ctx, cts[2], pb.diags, pb.keys, *split)[0])
+    assert_same(outs[2].numpy(), want, "autotuned batch item vs oracle")
+    mixed, _ = _encrypt_many(pb, [4, 3], 510)
+    with pytest.raises(binding.CkksError) as e:
+        g.autotune_batch("th", [g.ct_from_host(np.stack(c)) for c in mixed], f, 2)
+    assert e.value.status == 1
