@@ -579,8 +579,9 @@ def run_uneven(args, dist: Dist):
     """128 LTs per step at N = 2^16: diagonal counts from {16, 64, 256, 1024},
     offsets consecutive or strided by 2^k (k = 1..4, D 2^k <= N/2), levels
     uniform in 6..24 (seed 3); one matrix per distinct (D, stride) shape shared
-    by the LTs of that shape; one split per shape from the cost model; one
-    recorded lt_eval_batch per step against 128 sequential lt_eval calls."""
+    by the LTs of that shape; one split per (shape, level), picked by the
+    measuring autotuner among the cost model's best candidates; one recorded
+    lt_eval_batch per step against 128 sequential lt_eval calls."""
     import numpy as np
     import torch
     from paper_2605_17222_gb300 import binding, synth
@@ -597,9 +598,15 @@ def run_uneven(args, dist: Dist):
         stride = 1 if rng.random() < 0.5 or not ks else 1 << int(rng.choice(ks))
         items.append((d, stride, int(rng.integers(6, 25))))
     shapes = sorted({(d, st) for d, st, _ in items})
-    split_of = {sh: g.choose_split("th", ps.L, sh[0]) for sh in shapes}
-    rots = sorted({(r * 1) % (ps.n // 2) for (d, st) in shapes
-                   for r in g.required_rotations("th", split_of[(d, st)], d, st)})
+    combos = sorted({(d, st, lv) for d, st, lv in items})
+    # keys for the cost model's best candidates of every (shape, level) present,
+    # as many candidates as keep the key set within 300 keys (176 MB each)
+    for ncand in (3, 2, 1):
+        cands = {c: g.candidate_splits("th", c[2], c[0], ncand) for c in combos}
+        rots = sorted({r for (d, st, lv), cs in cands.items() for sp in cs
+                       for r in g.required_rotations("th", sp, d, st)})
+        if len(rots) <= 300:
+            break
     for r in rots:
         t = synth.uniform_mod_device(SEED, f"key/{r}", ps.moduli, ps.n, count=2 * g.beta_max, device=device)
         g.upload_rotation_key_device(r, t)
@@ -615,7 +622,12 @@ def run_uneven(args, dist: Dist):
                                               device=device), lv) for n, (_, _, lv) in enumerate(items)]
     outs = [g.ct_empty(lv - 1) for (_, _, lv) in items]
     fs = [mats[(d, st)] for d, st, _ in items]
-    sps = [split_of[(d, st)] for d, st, _ in items]
+    # the measuring autotuner, per (shape, level): times the candidates on one of the LTs
+    split_of = {}
+    for (d, st, lv), cs in cands.items():
+        sample = next(c for c, it in zip(cts, items) if it == (d, st, lv))
+        split_of[(d, st, lv)] = g.autotune("th", sample, mats[(d, st)], len(cs))[0] if len(cs) > 1 else cs[0]
+    sps = [split_of[it] for it in items]
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
 
@@ -654,7 +666,9 @@ def run_uneven(args, dist: Dist):
         "config": {"workload": f"uneven batch: {n_lt} LTs, N=2^16, D from {{16,64,256,1024}}, consecutive or "
                                f"2^k-strided offsets, levels 6..24 (seed 3), one matrix per (D, stride) shape; one "
                                f"recorded lt_eval_batch per step",
-                   "shapes": {f"{d}/{st}": list(split_of[(d, st)]) for d, st in shapes},
+                   "splits": {f"{d}/{st}@{lv}": list(sp) for (d, st, lv), sp in sorted(split_of.items())},
+                   "split_choice": f"lt_autotune per (shape, level) over the cost model's {ncand} best "
+                                   f"({len(rots)} keys resident)",
                    "keys": len(rots)},
         "sequential_lt_per_s": round(dist.world * n_lt * steps / (ms_seq / 1e3), 3),
         "speedup_vs_sequential": round(ms_seq / ms_graph, 3),
