@@ -203,6 +203,18 @@ typedef struct lt_graph lt_graph;
 ckks_status lt_graph_create(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* in, const ckks_diags* const* f,
                             const lt_algo* algos, const lt_split* splits, ckks_ct* const* out, lt_graph** graph);
 ckks_status lt_graph_launch(lt_graph* graph, void* stream);
+/* Recording of any sequence of LT calls (a chain, several batches, single
+ * LTs).  lt_graph_begin starts capturing `stream` (a created stream, not the
+ * legacy default stream; thread-local capture mode); the lt_eval,
+ * lt_eval_batch and lt_eval_chain calls this thread then queues on `stream`
+ * are recorded instead of run, and lt_graph_end returns them as one graph
+ * for lt_graph_launch.  Every recorded call must have run once before with
+ * the same shapes: first use sets up per-level tables with synchronous copies
+ * that a recording cannot hold, and such a call fails (CKKS_ECUDA) and leaves
+ * the recording invalid, so that lt_graph_end fails too.  lt_graph_end always
+ * ends the capture.  The same lifetime rules as for lt_graph_create apply. */
+ckks_status lt_graph_begin(ckks_ctx* ctx, void* stream);
+ckks_status lt_graph_end(ckks_ctx* ctx, void* stream, lt_graph** graph);
 ckks_status lt_graph_destroy(lt_graph* graph);
 
 /* Rotation amounts (mod N/2, ascending, multiples of stride) whose keys the

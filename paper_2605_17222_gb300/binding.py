@@ -88,6 +88,8 @@ def lib():
         "ckks_device_status": [P],
         "lt_graph_create": [P, U32, P, P, P, P, P, PP],
         "lt_graph_launch": [P, P],
+        "lt_graph_begin": [P, P],
+        "lt_graph_end": [P, P, PP],
         "lt_graph_destroy": [P],
         "ckks_selftest_bounded_wait": [P, U32, P],
     }
@@ -194,7 +196,7 @@ class Diagonals:
 
 
 class RecordedBatch:
-    """A replayable lt_eval_batch (lt_graph_*)."""
+    """A replayable recording of LT calls (lt_graph_create, or lt_graph_begin/end)."""
 
     def __init__(self, handle, outs, keep):
         self.h, self.outs, self._keep = handle, outs, keep
@@ -407,6 +409,17 @@ class Context:
         h = ctypes.c_void_p()
         check(lib().lt_graph_create(self.h, n, arr(cts), arr(diags), al, sp, arr(outs), ctypes.byref(h)))
         return RecordedBatch(h, outs, (cts, diags))
+
+    def graph_begin(self, stream) -> None:
+        """Start recording the LT calls queued on `stream` (a torch.cuda.Stream)."""
+        check(lib().lt_graph_begin(self.h, _stream(stream)))
+
+    def graph_end(self, stream, keep=()) -> "RecordedBatch":
+        """Stop recording `stream`; the recorded calls as one replayable graph.
+        `keep` holds the objects the graph reads or writes alive with it."""
+        h = ctypes.c_void_p()
+        check(lib().lt_graph_end(self.h, _stream(stream), ctypes.byref(h)))
+        return RecordedBatch(h, None, tuple(keep))
 
     # ----------------------------------------------------------- steps (device tensors)
     def ntt(self, poly, level: int, ext: bool, inverse: bool, stream=None):

@@ -1626,6 +1626,40 @@ ckks_status lt_graph_create(ckks_ctx* ctx, uint32_t count, const ckks_ct* const*
     return rc;
 }
 
+ckks_status lt_graph_begin(ckks_ctx* ctx, void* stream) {
+    return guarded([&] {
+        if (!ctx) fail(CKKS_EINVAL, "null argument");
+        if (!stream) fail(CKKS_EINVAL, "the legacy default stream cannot be recorded; pass a created stream");
+        CK(cudaSetDevice(ctx->device));
+        CK(cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal));
+    });
+}
+
+ckks_status lt_graph_end(ckks_ctx* ctx, void* stream, lt_graph** graph) {
+    cudaGraph_t g = nullptr;
+    lt_graph* gr = nullptr;
+    ckks_status rc = guarded([&] {
+        if (!ctx || !stream || !graph) fail(CKKS_EINVAL, "null argument");
+        *graph = nullptr;
+        CK(cudaSetDevice(ctx->device));
+        // ends the capture even when a recorded call failed (the graph is then invalid)
+        CK(cudaStreamEndCapture((cudaStream_t)stream, &g));
+        gr = new lt_graph{ctx};
+        gr->graph = g;
+        g = nullptr;
+        CK(cudaGraphInstantiate(&gr->exec, gr->graph, 0));
+        *graph = gr;
+        gr = nullptr;
+    });
+    if (g) cudaGraphDestroy(g);
+    if (gr) {
+        if (gr->exec) cudaGraphExecDestroy(gr->exec);
+        if (gr->graph) cudaGraphDestroy(gr->graph);
+        delete gr;
+    }
+    return rc;
+}
+
 ckks_status lt_graph_launch(lt_graph* graph, void* stream) {
     return guarded([&] {
         if (!graph) fail(CKKS_EINVAL, "null argument");

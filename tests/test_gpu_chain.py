@@ -151,3 +151,36 @@ def test_full_size_coeff_to_slot_chain():
     err = np.abs(cp.decrypt((got[0], got[1])) - cp.expected())
     assert np.median(err) < 1e-7
     assert np.max(err) < 5e-5
+
+
+def test_recorded_chain_replays_on_new_inputs():
+    """lt_graph_begin/end records an lt_eval_chain queued on a created stream;
+    replays recompute from the input's current contents, bit-exact with the
+    oracle; the legacy default stream is refused."""
+    import torch
+    from paper_2605_17222_gb300 import binding
+    cp = make_chain_problem("toy", 2, "stc", [4, 4, 3], [(2, 2, 8), (4, 4, 2), (2, 2, 2)])
+    g = gpu_context("toy")
+    fs = upload_chain(g, cp)
+    ct = g.ct_from_host(np.stack(cp.ct))
+    out = g.ct_empty(1)
+    st = torch.cuda.Stream()
+    g.lt_eval_chain(ct, fs, splits=cp.splits, out=out, stream=st)  # first use sets up the tables
+    st.synchronize()
+    g.graph_begin(st)
+    g.lt_eval_chain(ct, fs, splits=cp.splits, out=out, stream=st)
+    rec = g.graph_end(st, keep=(ct, out, fs))
+    out.tensor.zero_()
+    rec.launch(st)
+    st.synchronize()
+    assert_same(out.numpy(), np.stack(olt.lt_chain(cp.ctx, cp.ct, cp.stages(), cp.keys)), "replay 1")
+    ct2 = cp.ctx.encrypt(cp.z[::-1].copy(), cp.s, cp.level, cp.scale, 41, stream="replay")
+    ct.tensor.copy_(torch.from_numpy(np.stack(ct2).view(np.int64)).cuda())
+    torch.cuda.synchronize()
+    rec.launch(st)
+    st.synchronize()
+    assert_same(out.numpy(), np.stack(olt.lt_chain(cp.ctx, ct2, cp.stages(), cp.keys)), "replay 2")
+    rec.close()
+    with pytest.raises(binding.CkksError) as e:
+        g.graph_begin(0)
+    assert e.value.status == 1
