@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -140,6 +141,13 @@ struct ckks_ctx {
     std::map<std::tuple<int, u32, u32, int32_t, int32_t>, lt_split> tuned;  // (algo, level, D, stride, offset0 mod N/2)
     std::mutex mu;
     size_t bytes = 0;
+    // fork/join lanes of lt_eval_batch: independent groups run on the caller's
+    // stream and up to FORK_LANES - 1 more, so that one group's NTT-bound
+    // phases overlap another's HBM-bound diagonal multiply-accumulate
+    static constexpr u32 FORK_LANES = 4;
+    std::mutex fork_mu;  // the lanes' streams and events are shared by all callers
+    cudaStream_t lane[FORK_LANES - 1] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[FORK_LANES - 1] = {};
 
     u32 beta(u32 level) const { return (level + alpha - 1) / alpha; }
     u32 slots() const { return N / 2; }
@@ -1090,6 +1098,11 @@ ckks_status ckks_ctx_destroy(ckks_ctx* ctx) {
         }
         for (DevBuf* b : {&ctx->d_mods, &ctx->d_psi, &ctx->d_ipsi, &ctx->d_lift, &ctx->d_lift_sh, &ctx->d_err})
             cudaFree(b->p);
+        for (u32 i = 0; i + 1 < ckks_ctx::FORK_LANES; i++) {
+            if (ctx->lane[i]) cudaStreamDestroy(ctx->lane[i]);
+            if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
+        }
+        if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
         delete ctx;
     });
 }
@@ -1338,7 +1351,7 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
         for (const lt_split& sp : cand) {
             lt_eval_impl(ctx, sample, f, algo, &sp, out, st, nullptr);  // warm-up (tables, attributes)
             CK(cudaEventRecord(e0, st));
-            const int reps = 3;
+            const int reps = 5;  // candidates are often within a few percent of each other
             for (int r = 0; r < reps; r++) lt_eval_impl(ctx, sample, f, algo, &sp, out, st, nullptr);
             CK(cudaEventRecord(e1, st));
             CK(cudaEventSynchronize(e1));
@@ -1508,12 +1521,23 @@ ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* i
         }
         CK(cudaSetDevice(ctx->device));
         // group the hoisted LTs by (diagonals, level, split); BSGS runs one by one
+        struct Unit {
+            double cost;  // model time of the unit's LTs
+            std::function<void(cudaStream_t)> run;
+        };
+        std::vector<Unit> units;
         std::vector<bool> done(count, false);
         for (u32 a = 0; a < count; a++) {
             if (done[a]) continue;
             const Item& ia = items[a];
+            const u32 lva = in[ia.idx]->level;
+            const double one = model_time(ctx, ia.algo, lva, f[ia.idx]->n_diag, ia.sp);
             if (ia.algo == LT_BSGS) {
-                lt_eval_impl(ctx, in[ia.idx], f[ia.idx], ia.algo, &ia.sp, out[ia.idx], st, nullptr);
+                const ckks_ct* ci = in[ia.idx];
+                const ckks_diags* fi = f[ia.idx];
+                ckks_ct* oi = out[ia.idx];
+                const lt_split spi = ia.sp;
+                units.push_back(Unit{one, [=](cudaStream_t s) { lt_eval_impl(ctx, ci, fi, LT_BSGS, &spi, oi, s, nullptr); }});
                 done[a] = true;
                 continue;
             }
@@ -1532,7 +1556,35 @@ ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* i
                                      out[ib.idx]->d + (size_t)(level - 1) * ctx->N});
                 done[b] = true;
             }
-            sched_th_batch(ctx, in[ia.idx]->level, group, f[ia.idx], n1, n2, n3, st);
+            const ckks_diags* fa = f[ia.idx];
+            units.push_back(Unit{one * group.size(), [=](cudaStream_t s) {
+                                     sched_th_batch(ctx, lva, group, fa, n1, n2, n3, s);
+                                 }});
+        }
+        if (units.size() <= 1) {
+            for (Unit& u : units) u.run(st);
+        } else {
+            // fork: the biggest units first, each onto the least-loaded lane; join on the caller's stream
+            std::lock_guard<std::mutex> g(ctx->fork_mu);
+            const u32 nl = (u32)std::min<size_t>(units.size(), ckks_ctx::FORK_LANES);
+            if (!ctx->fork_ev) CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+            for (u32 i = 0; i + 1 < nl; i++) {
+                if (!ctx->lane[i]) CK(cudaStreamCreateWithFlags(&ctx->lane[i], cudaStreamNonBlocking));
+                if (!ctx->join_ev[i]) CK(cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming));
+            }
+            CK(cudaEventRecord(ctx->fork_ev, st));
+            for (u32 i = 0; i + 1 < nl; i++) CK(cudaStreamWaitEvent(ctx->lane[i], ctx->fork_ev, 0));
+            std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.cost > y.cost; });
+            std::vector<double> load(nl, 0.0);
+            for (Unit& u : units) {
+                const u32 w = (u32)(std::min_element(load.begin(), load.end()) - load.begin());
+                load[w] += u.cost;
+                u.run(w == 0 ? st : ctx->lane[w - 1]);
+            }
+            for (u32 i = 0; i + 1 < nl; i++) {
+                CK(cudaEventRecord(ctx->join_ev[i], ctx->lane[i]));
+                CK(cudaStreamWaitEvent(st, ctx->join_ev[i], 0));
+            }
         }
         CK(cudaGetLastError());
     });
