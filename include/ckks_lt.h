@@ -212,7 +212,11 @@ ckks_status lt_graph_launch(lt_graph* graph, void* stream);
  * the same shapes: first use sets up per-level tables with synchronous copies
  * that a recording cannot hold, and such a call fails (CKKS_ECUDA) and leaves
  * the recording invalid, so that lt_graph_end fails too.  lt_graph_end always
- * ends the capture.  The same lifetime rules as for lt_graph_create apply. */
+ * ends the capture.  The capture is thread-local: while a thread records, it
+ * may not queue LT calls on other streams (CUDA forbids the stream-ordered
+ * allocations they make); other threads may, and a batch forked over lanes
+ * uses lanes of its own caller stream, never those of the recorded stream.
+ * The same lifetime rules as for lt_graph_create apply. */
 ckks_status lt_graph_begin(ckks_ctx* ctx, void* stream);
 ckks_status lt_graph_end(ckks_ctx* ctx, void* stream, lt_graph** graph);
 ckks_status lt_graph_destroy(lt_graph* graph);

@@ -144,10 +144,15 @@ struct ckks_ctx {
     // fork/join lanes of lt_eval_batch: independent groups run on the caller's
     // stream and up to FORK_LANES - 1 more, so that one group's NTT-bound
     // phases overlap another's HBM-bound diagonal multiply-accumulate
+    // Each caller stream has its own lanes, so that a stream being recorded
+    // into a graph captures only its own lanes, never another caller's work.
     static constexpr u32 FORK_LANES = 4;
-    std::mutex fork_mu;  // the lanes' streams and events are shared by all callers
-    cudaStream_t lane[FORK_LANES - 1] = {};
-    cudaEvent_t fork_ev = nullptr, join_ev[FORK_LANES - 1] = {};
+    struct Lanes {
+        cudaStream_t s[FORK_LANES - 1] = {};
+        cudaEvent_t fork = nullptr, join[FORK_LANES - 1] = {};
+    };
+    std::mutex fork_mu;
+    std::map<cudaStream_t, Lanes> lanes;
 
     u32 beta(u32 level) const { return (level + alpha - 1) / alpha; }
     u32 slots() const { return N / 2; }
@@ -297,6 +302,25 @@ struct Arena {
         for (void* p : blocks) cudaFreeAsync(p, st);
     }
 };
+
+// The fork lanes of one caller stream (lt_eval_batch).
+void destroy_lanes(ckks_ctx::Lanes& ln) {
+    for (u32 i = 0; i + 1 < ckks_ctx::FORK_LANES; i++) {
+        if (ln.s[i]) cudaStreamDestroy(ln.s[i]);
+        if (ln.join[i]) cudaEventDestroy(ln.join[i]);
+    }
+    if (ln.fork) cudaEventDestroy(ln.fork);
+    ln = ckks_ctx::Lanes{};
+}
+// Drops the lanes of a private stream the library is about to destroy (its
+// work must be complete).
+void release_lanes(ckks_ctx* C, cudaStream_t st) {
+    std::lock_guard<std::mutex> g(C->fork_mu);
+    auto it = C->lanes.find(st);
+    if (it == C->lanes.end()) return;
+    destroy_lanes(it->second);
+    C->lanes.erase(it);
+}
 
 // ------------------------------------------------------------------ key switching steps
 // Decompose (Fig. 1, Eq. 3) of `count` polynomials at once: c_i [level][N]
@@ -1098,11 +1122,7 @@ ckks_status ckks_ctx_destroy(ckks_ctx* ctx) {
         }
         for (DevBuf* b : {&ctx->d_mods, &ctx->d_psi, &ctx->d_ipsi, &ctx->d_lift, &ctx->d_lift_sh, &ctx->d_err})
             cudaFree(b->p);
-        for (u32 i = 0; i + 1 < ckks_ctx::FORK_LANES; i++) {
-            if (ctx->lane[i]) cudaStreamDestroy(ctx->lane[i]);
-            if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
-        }
-        if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+        for (auto& kv : ctx->lanes) destroy_lanes(kv.second);
         delete ctx;
     });
 }
@@ -1372,7 +1392,10 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (st) cudaStreamDestroy(st);
+    if (st) {
+        release_lanes(ctx, st);
+        cudaStreamDestroy(st);
+    }
     return rc;
 }
 
@@ -1433,7 +1456,10 @@ ckks_status lt_autotune_batch(ckks_ctx* ctx, lt_algo algo, uint32_t count, const
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (st) cudaStreamDestroy(st);
+    if (st) {
+        release_lanes(ctx, st);
+        cudaStreamDestroy(st);
+    }
     return rc;
 }
 
@@ -1567,23 +1593,24 @@ ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* i
             // fork: the biggest units first, each onto the least-loaded lane; join on the caller's stream
             std::lock_guard<std::mutex> g(ctx->fork_mu);
             const u32 nl = (u32)std::min<size_t>(units.size(), ckks_ctx::FORK_LANES);
-            if (!ctx->fork_ev) CK(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+            ckks_ctx::Lanes& ln = ctx->lanes[st];
+            if (!ln.fork) CK(cudaEventCreateWithFlags(&ln.fork, cudaEventDisableTiming));
             for (u32 i = 0; i + 1 < nl; i++) {
-                if (!ctx->lane[i]) CK(cudaStreamCreateWithFlags(&ctx->lane[i], cudaStreamNonBlocking));
-                if (!ctx->join_ev[i]) CK(cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming));
+                if (!ln.s[i]) CK(cudaStreamCreateWithFlags(&ln.s[i], cudaStreamNonBlocking));
+                if (!ln.join[i]) CK(cudaEventCreateWithFlags(&ln.join[i], cudaEventDisableTiming));
             }
-            CK(cudaEventRecord(ctx->fork_ev, st));
-            for (u32 i = 0; i + 1 < nl; i++) CK(cudaStreamWaitEvent(ctx->lane[i], ctx->fork_ev, 0));
+            CK(cudaEventRecord(ln.fork, st));
+            for (u32 i = 0; i + 1 < nl; i++) CK(cudaStreamWaitEvent(ln.s[i], ln.fork, 0));
             std::stable_sort(units.begin(), units.end(), [](const Unit& x, const Unit& y) { return x.cost > y.cost; });
             std::vector<double> load(nl, 0.0);
             for (Unit& u : units) {
                 const u32 w = (u32)(std::min_element(load.begin(), load.end()) - load.begin());
                 load[w] += u.cost;
-                u.run(w == 0 ? st : ctx->lane[w - 1]);
+                u.run(w == 0 ? st : ln.s[w - 1]);
             }
             for (u32 i = 0; i + 1 < nl; i++) {
-                CK(cudaEventRecord(ctx->join_ev[i], ctx->lane[i]));
-                CK(cudaStreamWaitEvent(st, ctx->join_ev[i], 0));
+                CK(cudaEventRecord(ln.join[i], ln.s[i]));
+                CK(cudaStreamWaitEvent(st, ln.join[i], 0));
             }
         }
         CK(cudaGetLastError());
@@ -1674,7 +1701,10 @@ ckks_status lt_graph_create(ckks_ctx* ctx, uint32_t count, const ckks_ct* const*
         if (gr->graph) cudaGraphDestroy(gr->graph);
         delete gr;
     }
-    if (st) cudaStreamDestroy(st);
+    if (st) {
+        release_lanes(ctx, st);
+        cudaStreamDestroy(st);
+    }
     return rc;
 }
 

@@ -138,3 +138,54 @@ def test_batch_autotuner_picks_a_candidate_and_stays_exact():
     with pytest.raises(binding.CkksError) as e:
         g.autotune_batch("th", [g.ct_from_host(np.stack(c)) for c in mixed], f, 2)
     assert e.value.status == 1
+
+
+def test_recording_one_stream_leaves_another_streams_batch_alone():
+    """While one thread records stream S, another thread's batch on stream T,
+    forked over T's own lanes, runs at once and is not captured; the graph
+    recorded on S replays S's batch only.  (The recording thread itself may not
+    queue work on other streams: thread-local capture forbids the allocations.)"""
+    import threading
+
+    import torch
+    pb = make_problem("toy", 0, 64)
+    ensure_keys(pb, "th", (4, 4, 4))
+    g = gpu_context("toy")
+    f = upload_problem(g, pb)
+    cts, _ = _encrypt_many(pb, [4, 3, 4, 3], 700)  # two levels: two groups, so the batch forks
+    ins = [g.ct_from_host(np.stack(ct)) for ct in cts]
+    args = dict(algos=["th"] * 4, splits=[(4, 4, 4)] * 4)
+    want = [o.numpy() for o in g.lt_eval_batch(ins, [f] * 4, **args)]
+    S, T = torch.cuda.Stream(), torch.cuda.Stream()
+    out_s = [g.ct_empty(c.level - 1) for c in ins]
+    out_t = [g.ct_empty(c.level - 1) for c in ins]
+    g.lt_eval_batch(ins, [f] * 4, outs=out_s, stream=S, **args)  # first use of each stream's lanes
+    g.lt_eval_batch(ins, [f] * 4, outs=out_t, stream=T, **args)
+    torch.cuda.synchronize()
+    for o in out_s + out_t:
+        o.tensor.zero_()
+    torch.cuda.synchronize()
+    errors = []
+
+    def other_thread():
+        try:
+            g.lt_eval_batch(ins, [f] * 4, outs=out_t, stream=T, **args)  # runs now
+            T.synchronize()
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    g.graph_begin(S)
+    g.lt_eval_batch(ins, [f] * 4, outs=out_s, stream=S, **args)  # recorded
+    th = threading.Thread(target=other_thread)
+    th.start()
+    th.join()
+    rec = g.graph_end(S, keep=(ins, out_s, f))
+    assert not errors, errors
+    for n, (o, w) in enumerate(zip(out_t, want)):
+        assert_same(o.numpy(), w, f"stream T item {n}")
+    assert not any(np.any(o.numpy()) for o in out_s)  # S's work was recorded, not run
+    rec.launch(S)
+    S.synchronize()
+    for n, (o, w) in enumerate(zip(out_s, want)):
+        assert_same(o.numpy(), w, f"replay item {n}")
+    rec.close()
