@@ -124,6 +124,7 @@ def param_set(name: str) -> ParamSet:
     toy  : N=2^12, Q = 50b + 3x40b, P = 1x60b, dnum 4 (functional toy, not secure)
     n16  : N=2^16, Q = 55b + 23x40b (24 limbs), P = 4x60b, dnum 6 (alpha 4, beta 6)
     n15  : N=2^15, Q = 50b + 15x40b (16 limbs), P = 3x60b, dnum 4 (alpha 4)
+    n14  : N=2^14, Q = 50b + 7x40b (8 limbs), P = 2x60b, dnum 4 (alpha 2)
     setA : the paper's Set-A shape, N=2^13, L+1=5, alpha=5, beta=1, 54-bit words
     setB : the paper's Set-B shape, N=2^15, L+1=16, alpha=8, beta=2, 54-bit words
     """
@@ -136,6 +137,8 @@ def param_set(name: str) -> ParamSet:
         ps = make_params("n16", 16, [55] + [40] * 23, [60] * 4, 6)
     elif name == "n15":
         ps = make_params("n15", 15, [50] + [40] * 15, [60] * 3, 4)
+    elif name == "n14":  # covers the N = 2^14 transform shape (7 + 7 NTT stages per pass)
+        ps = make_params("n14", 14, [50] + [40] * 7, [60] * 2, 4)
     elif name == "setA":
         ps = make_params("setA", 13, [54] * 5, [54] * 5, 1)
     elif name == "setB":

@@ -13,7 +13,7 @@ from gpu_common import assert_same
 
 pytestmark = pytest.mark.gpu
 
-SETS = ["toy", "n15", "n16"]
+SETS = ["toy", "setA", "n14", "n15", "n16"]  # every NTT shape, N = 2^12 .. 2^16
 _CACHE = {}
 
 
