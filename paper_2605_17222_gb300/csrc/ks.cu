@@ -330,6 +330,8 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
     const bool lift_limb = a.lift0 && t < a.level;
     const u64 lc = lift_limb ? a.lift_c[gmod] : 0, lsh = lift_limb ? a.lift_sh[gmod] : 0;
     constexpr u32 RB = RUN * 8;  // bytes per run
+    const bool fold = m.q < (1ull << 41) && beta <= 8;
+    const u64 c63 = fold ? (1ull << 63) % m.q : 0, c64 = fold ? (0 - m.q) % m.q : 0;  // 2^63, 2^64 mod q
 
     // shared memory: NS stages of [K3 diag | beta digit | A | B] runs
     const u32 stage_runs = K3 + beta + 2;
@@ -449,9 +451,18 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
             } else {
                 add128(x0, st[(K3 + beta) * RUN + pm]);
             }
-            // partial reductions (values below 4q < 2^62) are enough to feed the products
-            av = reduce128_lazy(x0, m);
-            bv = reduce128_lazy(x1, m);
+            // partial reductions are enough to feed the products: below 4q < 2^62
+            // in general; for q < 2^41 (and beta <= 8, so x < 2^85) a fold
+            //   (x mod 2^63) + [bit 63] (2^63 mod q) + x_hi (2^64 mod q)  <  2^64
+            // is congruent to x, and 64 of its products with a word below q stay
+            // below 2^128 in the accumulators
+            if (fold) {
+                av = (x0.lo & ~(1ull << 63)) + ((x0.lo >> 63) ? c63 : 0) + x0.hi * c64;
+                bv = (x1.lo & ~(1ull << 63)) + ((x1.lo >> 63) ? c63 : 0) + x1.hi * c64;
+            } else {
+                av = reduce128_lazy(x0, m);
+                bv = reduce128_lazy(x1, m);
+            }
         }
 #pragma unroll
         for (int kk = 0; kk < K3; kk++) {
