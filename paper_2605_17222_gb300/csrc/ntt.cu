@@ -177,8 +177,9 @@ __device__ __forceinline__ u64 red2(u64 x, u64 q, u64 mu_hi) { return x - __umul
 // For moduli well below 2^64 the per-butterfly conditional subtraction that
 // keeps a lazy word bounded can be dropped inside a pass:
 //   CT: if both inputs are below B, (a + v, a - v + 2q) with v = b w mod q in
-//       [0, 2q) are both below B + 2q.  The 2 log N <= 32 stages of a forward
-//       transform from [0, q) stay below 33q, below 2^64 for q < 2^58.
+//       [0, 2q) are both below B + 2q.  The log N <= 16 stages of a forward
+//       transform from [0, 4q) (a lazily reduced basis conversion) stay below
+//       36q, below 2^64 for q < 2^58.
 //   GS: if both inputs are below M (a multiple of q), (a + b, (a - b + M) w
 //       mod q) are below 2M.  The <= 8 stages of one pass from [0, B) stay
 //       below 2^8 B; a pass starts from [0, q) (row) or [0, 2q) (column), so
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
             const u64* src = J.src + (size_t)(u + TPL * v) * C + col;
             U128 acc{0, 0};
             for (u32 j = 0; j < ns; j++) mac128(acc, src[(size_t)j * N], bc[j]);
-            sm[(u + TPL * v) * W + c] = reduce128(acc, m);
+            sm[(u + TPL * v) * W + c] = reduce128_lazy(acc, m);  // [0, 4q): both butterfly forms take it
         }
 #pragma unroll
         for (int v = 0; v < 16; v++) x[v] = sm[(u + TPL * v) * W + c];
@@ -283,7 +284,8 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
 #pragma unroll
         for (int v = 0; v < 16; v++) x[v] = J.src[(size_t)(u + TPL * v) * C + col];
     }
-    // words enter in [0, q); they leave below 4q (reducing) or 17q (growing)
+    // words enter below 4q; they leave below 4q (reducing) or 20q (growing: +2q per stage),
+    // and the row pass ends below 36q < 2^64 (q < 2^58)
     if (q < FWD_GROW_MAX) fwd_cols_stages<LOGS, true>(x, sm, u, c, tw, q);
     else fwd_cols_stages<LOGS, false>(x, sm, u, c, tw, q);
 #pragma unroll
@@ -348,7 +350,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__
         const u32 xi = u + TPL * v;
         const u64 y = sr[pad16(xi)];
         u64 val;
-        if (grow) {  // below 33q
+        if (grow) {  // below 36q
             val = red2(y, q, m.mu_hi);
             val = val >= q ? val - q : val;
         } else {  // below 4q
