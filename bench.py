@@ -187,6 +187,26 @@ def algorithmic_bytes(cls: str, split, level: int, k: int, beta: int, n_diag: in
     return None, None
 
 
+def algorithmic_bytes_for(algo: str, cls: str, split, level: int, k: int, beta: int, n_diag: int, N: int) -> tuple:
+    """algorithmic_bytes for any algorithm: DH(n1, n2) runs as TH(n1, 1, n2) and
+    the diagonal method as TH(1, D, 1); BSGS multiplies over Q only (K6 without
+    the P limbs or a middle layer) and switches keys once per rotation."""
+    if algo == "dh":
+        return algorithmic_bytes(cls, (split[0], 1, split[1]), level, k, beta, n_diag, N)
+    if algo == "diag":
+        return algorithmic_bytes(cls, (1, n_diag, 1), level, k, beta, n_diag, N)
+    if algo == "bsgs":
+        n1, n2 = split[0], split[1]
+        limb, ext = 8 * N, level + k
+        if cls == "diag_mac":
+            return limb * (n_diag * level + 2 * n1 * level + 2 * n2 * level), 1
+        if cls == "ks_inner":
+            rots = (n1 - 1) + (n2 - 1)
+            return rots * limb * (beta * ext + 2 * beta * ext + 2 * ext), rots
+        return None, None
+    return algorithmic_bytes(cls, split, level, k, beta, n_diag, N)
+
+
 def lt_compulsory_bytes(split, level: int, k: int, beta: int, n_diag: int, N: int) -> int:
     """Compulsory bytes of one LT: diagonals, distinct keys, ciphertext in and out."""
     n1, n2, n3 = split
@@ -383,7 +403,7 @@ def run_ours(args, dist: Dist):
         binding.profile_enable(c, False)
     tot = sum(v[0] for v in shares.values()) or 1.0
     dominant = max(shares, key=lambda c: shares[c][0])
-    if algo in ("th", "dh") and dominant not in ("diag_mac", "ks_inner"):
+    if dominant not in ("diag_mac", "ks_inner"):
         # the roofline below is defined for the HBM-streaming kernels
         dominant = max(("diag_mac", "ks_inner"), key=lambda c: shares[c][0])
 
@@ -434,7 +454,7 @@ def run_ours(args, dist: Dist):
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
-    b_lt, n_lt = algorithmic_bytes(dominant, split3, LEVEL, ps.k, beta, D, ps.n)
+    b_lt, n_lt = algorithmic_bytes_for(algo, dominant, split3, LEVEL, ps.k, beta, D, ps.n)
     roof = None
     if b_lt and dom_n:
         per_launch = b_lt / n_lt
@@ -454,8 +474,9 @@ def run_ours(args, dist: Dist):
         "config": {"workload": f"single LT: N=2^16, level {LEVEL} (Q = 55b + 23x40b), 4x60b special primes, "
                                f"dnum 6, {D} consecutive diagonals, one ciphertext at the top level",
                    "algo": algo, "split": list(split3), "parallelism": f"replicas x{dist.world}",
-                   "split_choice": "given" if args.split else f"autotuned over the cost model's best candidates "
-                                                               f"({tuned_ms:.3f} ms when measured)",
+                   "split_choice": ("given" if args.split else "the diagonal method has one split" if tuned_ms is None
+                                    else f"autotuned over the cost model's best candidates ({tuned_ms:.3f} ms "
+                                         f"when measured)"),
                    "l2": "inputs larger than L2 (keys + diagonals resident, > 6 GB per step); no flush"},
         "hbm_roofline_lt": (None if lt_bytes is None else {
             "compulsory_bytes": lt_bytes, "achieved_gbs": round(lt_bytes / (max_ms / args.steps / 1e3) / 1e9, 1),
