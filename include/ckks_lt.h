@@ -98,9 +98,12 @@ ckks_status ckks_ctx_destroy(ckks_ctx* ctx);
  * equal beta_max*2*(L+k)*N.  The same key serves every algorithm and split:
  * the hoisted form swk~_r = phi_{-r}(swk_r) of Algorithms 1-2 is applied as
  * an index gather on the digits.  r is taken mod N/2; replacing a key is
- * allowed when no queued work uses it. */
+ * allowed when no queued work uses it.  The library stores the key with its
+ * two components interleaved per word ([beta_max][L+k][N] pairs), so that
+ * every kernel reads one 16-byte word per digit word; the upload converts. */
 ckks_status ckks_upload_rotation_key(ckks_ctx* ctx, int32_t r, const uint64_t* host, size_t n_words);
-/* Same, from a device buffer the library copies (stream-ordered). */
+/* Same, from a device buffer the library reads in stream order on `stream`
+ * (the conversion is a kernel there; `dev` must stay valid until it ran). */
 ckks_status ckks_upload_rotation_key_device(ckks_ctx* ctx, int32_t r, const uint64_t* dev,
                                             size_t n_words, void* stream);
 int ckks_has_rotation_key(const ckks_ctx* ctx, int32_t r);

@@ -1138,8 +1138,19 @@ static void put_key(ckks_ctx* ctx, int32_t r, const uint64_t* src, size_t n_word
     if (it != ctx->keys.end()) d = it->second;
     else d = ctx->dalloc(n_words);
     ctx->keys[rk] = d;
-    if (kind == cudaMemcpyHostToDevice) CK(cudaMemcpy(d, src, n_words * 8, kind));
-    else CK(cudaMemcpyAsync(d, src, n_words * 8, kind, st));
+    // stored with the two components interleaved per word (one 16-byte load per digit word)
+    const size_t plane = (size_t)(ctx->L + ctx->K) * ctx->N;
+    if (kind == cudaMemcpyHostToDevice) {
+        u64* tmp = ctx->dalloc(n_words);
+        CK(cudaMemcpy(tmp, src, n_words * 8, kind));
+        launch_interleave_key(tmp, d, plane, ctx->beta_max, 0);
+        CK(cudaGetLastError());
+        CK(cudaDeviceSynchronize());
+        ctx->dfree(tmp, n_words);
+    } else {
+        launch_interleave_key(src, d, plane, ctx->beta_max, st);
+        CK(cudaGetLastError());
+    }
 }
 
 ckks_status ckks_upload_rotation_key(ckks_ctx* ctx, int32_t r, const uint64_t* host, size_t n_words) {

@@ -92,6 +92,12 @@ struct KsMultiArgs {
 };
 void launch_ks_multi(const KsMultiArgs& a, cudaStream_t st);
 
+// Rotation keys in the library's layout: the user's [beta_max][2][L+k][N]
+// with the two components interleaved per word, [beta_max][L+k][N] x 2.
+// Every kernel that reads a key reads one 16-byte word per (digit, limb,
+// position).  plane = (L+k) N.
+void launch_interleave_key(const u64* in, u64* out, size_t plane, u32 beta_max, cudaStream_t st);
+
 // Many independent K4 products (overwrite form, x0 lifted from a Q
 // polynomial) in one launch: entry e reads digits, key and x0 and writes
 // out0/out1.  Entries that share a key are adjacent in the grid.

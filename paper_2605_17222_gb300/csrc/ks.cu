@@ -30,13 +30,13 @@ __global__ void __launch_bounds__(THREADS) k_ks_inner(const __grid_constant__ Ks
     const u32 gmod = t < a.level ? t : a.L + (t - a.level);
     const ModC m = a.mods[gmod];
     const u32 src = a.gal ? auto_src(s, a.gal, a.log_n) : s;
-    const size_t key_b = 2ull * (a.L + kp) * N;
+    const size_t plane = (size_t)(a.L + kp) * N;  // key words per digit (interleaved components)
     U128 acc0{0, 0}, acc1{0, 0};
     for (u32 b = 0; b < a.beta; b++) {
         const u64 d = a.digits[((size_t)b * a.ext + t) * N + src];
-        const u64* kb = a.key + b * key_b + (size_t)gmod * N + s;
-        mac128(acc0, d, kb[0]);
-        mac128(acc1, d, kb[(size_t)(a.L + kp) * N]);
+        const ulonglong2 kv = ((const ulonglong2*)a.key)[b * plane + (size_t)gmod * N + s];
+        mac128(acc0, d, kv.x);
+        mac128(acc1, d, kv.y);
     }
     if (a.x0_mode == 1) {
         add128(acc0, a.x0[(size_t)t * N + src]);
@@ -62,18 +62,19 @@ __global__ void __launch_bounds__(THREADS) k_ks_multi(const __grid_constant__ Ks
     const u32 kp = a.ext - a.level;
     const u32 gmod = t < a.level ? t : a.L + (t - a.level);
     const ModC m = a.mods[gmod];
-    const size_t key_b = 2ull * (a.L + kp) * N, key_c = (size_t)(a.L + kp) * N;
+    const size_t plane = (size_t)(a.L + kp) * N;  // key words per digit (interleaved components)
     const size_t o = (size_t)t * N + s;
     U128 acc0{a.out0[o], 0}, acc1{a.out1[o], 0};
     for (u32 k = 0; k < a.count; k++) {
         const u32 src = auto_src(s, a.gal[k], a.log_n);
         const u64* D = a.digits[k] + (size_t)t * N + src;
-        const u64* K = a.keys[k] + (size_t)gmod * N + s;
+        const ulonglong2* K = (const ulonglong2*)a.keys[k] + (size_t)gmod * N + s;
         add128(acc0, a.x0[k][(size_t)t * N + src]);
         for (u32 b = 0; b < a.beta; b++) {
             const u64 d = D[(size_t)b * a.ext * N];
-            mac128(acc0, d, K[b * key_b]);
-            mac128(acc1, d, K[b * key_b + key_c]);
+            const ulonglong2 kv = K[b * plane];
+            mac128(acc0, d, kv.x);
+            mac128(acc1, d, kv.y);
         }
         // keep the running sums bounded: one partial reduction per giant index
         acc0 = U128{reduce128_lazy(acc0, m), 0};
@@ -94,13 +95,13 @@ __global__ void __launch_bounds__(THREADS) k_ks_batch(const __grid_constant__ Ks
     const u32 gmod = t < a.level ? t : a.L + (t - a.level);
     const ModC m = a.mods[gmod];
     const u32 src = E.gal ? auto_src(s, E.gal, a.log_n) : s;
-    const size_t key_b = 2ull * (a.L + kp) * N;
+    const size_t plane = (size_t)(a.L + kp) * N;  // key words per digit (interleaved components)
     U128 acc0{0, 0}, acc1{0, 0};
     for (u32 b = 0; b < a.beta; b++) {
         const u64 d = E.digits[((size_t)b * a.ext + t) * N + src];
-        const u64* kb = E.key + b * key_b + (size_t)gmod * N + s;
-        mac128(acc0, d, kb[0]);
-        mac128(acc1, d, kb[(size_t)(a.L + kp) * N]);
+        const ulonglong2 kv = ((const ulonglong2*)E.key)[b * plane + (size_t)gmod * N + s];
+        mac128(acc0, d, kv.x);
+        mac128(acc1, d, kv.y);
     }
     if (t < a.level) add128(acc0, mul_shoup(E.x0[(size_t)t * N + src], a.lift_c[gmod], a.lift_sh[gmod], m.q));
     const size_t o = (size_t)t * N + s;
@@ -140,8 +141,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_diag_mac(const __grid_constant__
     const u32 drow = t < a.level ? t : a.diag_level + (t - a.level);
     const ModC m = a.mods[gmod];
     const size_t dstride = (size_t)(a.diag_level + a.k_p) * N;
-    const size_t key_b = 2ull * (a.L + a.k_p) * N;
-    const size_t key_c = (size_t)(a.L + a.k_p) * N;
+    const size_t plane = (size_t)(a.L + a.k_p) * N;  // key words per digit (interleaved components)
     const size_t dig_b = (size_t)a.ext * N;
     const size_t tN = (size_t)t * N;
     const u32 n1n2 = a.n1 * a.n2;
@@ -165,13 +165,14 @@ __global__ void __launch_bounds__(THREADS, 2) k_diag_mac(const __grid_constant__
 
     for (u32 j = 0; j < a.n2; j++) {
         const u32 src = j ? auto_src(s, a.gal_mid[j], a.log_n) : s;
-        const u64* key = j ? a.keys[j] + (size_t)gmod * N + s : nullptr;
+        const ulonglong2* key = j ? (const ulonglong2*)a.keys[j] + (size_t)gmod * N + s : nullptr;
         if (j && small_beta) {
 #pragma unroll
             for (int b = 0; b < MAXB; b++) {
                 if (b < (int)beta) {
-                    sk[(2 * b) * THREADS] = key[b * key_b];
-                    sk[(2 * b + 1) * THREADS] = key[b * key_b + key_c];
+                    const ulonglong2 kv = key[b * plane];
+                    sk[(2 * b) * THREADS] = kv.x;
+                    sk[(2 * b + 1) * THREADS] = kv.y;
                 }
             }
         }
@@ -209,8 +210,9 @@ __global__ void __launch_bounds__(THREADS, 2) k_diag_mac(const __grid_constant__
                 } else {
                     for (u32 b = 0; b < beta; b++) {
                         const u64 dv = D[b * dig_b];
-                        mac128(x0, dv, key[b * key_b]);
-                        mac128(x1, dv, key[b * key_b + key_c]);
+                        const ulonglong2 kv = key[b * plane];
+                        mac128(x0, dv, kv.x);
+                        mac128(x1, dv, kv.y);
                     }
                 }
                 add128(x0, lifted ? mul_shoup(xa, lc, lsh, m.q) : xa);
@@ -321,8 +323,7 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
     const u32 drow = t < a.level ? t : a.diag_level + (t - a.level);
     const ModC m = a.mods[gmod];
     const size_t dstride = (size_t)(a.diag_level + a.k_p) * N;
-    const size_t key_b = 2ull * (a.L + a.k_p) * N;
-    const size_t key_c = (size_t)(a.L + a.k_p) * N;
+    const size_t plane = (size_t)(a.L + a.k_p) * N;  // key words per digit (interleaved components)
     const size_t dig_b = (size_t)a.ext * N;
     const size_t tN = (size_t)t * N;
     const u32 n1 = a.n1, n2 = a.n2, n1n2 = n1 * n2;
@@ -406,11 +407,12 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
         if (j > 0 && i == 0) {
             // a new giant index: its key words (not gathered) come straight from
             // global memory; the loads overlap the wait for the stage below
-            const u64* ks = a.keys[j] + (size_t)gmod * N + s;
+            const ulonglong2* ks = (const ulonglong2*)a.keys[j] + (size_t)gmod * N + s;
 #pragma unroll
             for (int b = 0; b < KB; b++) {
-                k0[b] = b < (int)beta ? ks[b * key_b] : 0;
-                k1[b] = b < (int)beta ? ks[b * key_b + key_c] : 0;
+                const ulonglong2 kv = b < (int)beta ? ks[b * plane] : make_ulonglong2(0, 0);
+                k0[b] = kv.x;
+                k1[b] = kv.y;
             }
             pm = auto_src(s, a.gal_mid[j], a.log_n) % RUN;
         }
@@ -538,6 +540,22 @@ bool launch_staged(const DiagMacArgs& a, cudaStream_t st) {
 }
 
 }  // namespace
+
+// Switching keys are stored with their two components interleaved per word:
+// in [beta_max][2][L+k][N] -> out [beta_max][L+k][N] of (component 0, component 1).
+__global__ void k_interleave_key(const u64* __restrict__ in, ulonglong2* __restrict__ out, size_t plane,
+                                 size_t total) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const size_t b = i / plane, r = i - b * plane;
+    out[i] = make_ulonglong2(in[(2 * b) * plane + r], in[(2 * b + 1) * plane + r]);
+}
+
+void launch_interleave_key(const u64* in, u64* out, size_t plane, u32 beta_max, cudaStream_t st) {
+    const size_t total = plane * beta_max;
+    k_interleave_key<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(in, (ulonglong2*)out, plane, total);
+    count_launch();
+}
 
 void launch_wait_selftest(u32* err, u64 limit_ns, cudaStream_t st) {
     k_wait_selftest<<<1, 32, 0, st>>>(err, limit_ns);
