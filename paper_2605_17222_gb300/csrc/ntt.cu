@@ -176,25 +176,37 @@ __device__ __forceinline__ u64 red2(u64 x, u64 q, u64 mu_hi) { return x - __umul
 // ------------------------------------------------------------------ growing butterflies
 // For moduli well below 2^64 the per-butterfly conditional subtraction that
 // keeps a lazy word bounded can be dropped inside a pass:
-//   CT: if both inputs are below B, (a + v, a - v + 2q) with v = b w mod q in
-//       [0, 2q) are both below B + 2q.  The log N <= 16 stages of a forward
-//       transform from [0, 4q) (a lazily reduced basis conversion) stay below
-//       36q, below 2^64 for q < 2^58.
+//   CT: if both inputs are below B, (a + v, a - v + 4q) with v = b w mod q in
+//       [0, 4q) (a quotient estimate that may be 2 short, mul_shoup_approx)
+//       are both below B + 4q.  The log N <= 16 stages of a forward transform
+//       from [0, 4q) (a lazily reduced basis conversion) stay below 68q, below
+//       2^64 for q < 2^57.
 //   GS: if both inputs are below M (a multiple of q), (a + b, (a - b + M) w
 //       mod q) are below 2M.  The <= 8 stages of one pass from [0, B) stay
 //       below 2^8 B; a pass starts from [0, q) (row) or [0, 2q) (column), so
 //       everything stays below 2^9 q < 2^64 for q < 2^55.
 // Wider moduli (the 60-bit special primes) take the reducing butterflies.
-constexpr u64 FWD_GROW_MAX = 1ull << 58;
+constexpr u64 FWD_GROW_MAX = 1ull << 57;
 constexpr u64 INV_GROW_MAX = 1ull << 55;
+
+// b w mod q up to 4q, for any b < 2^64 (w < q, ws = floor(w 2^64 / q)).  Of
+// the four 32 x 32 partial products of b ws the quotient estimate keeps the
+// high one and the high halves of the two middle ones; what it drops carries
+// at most 2 into bit 64, so the estimate is below floor(b ws / 2^64) by at
+// most 2 and the remainder lies in [0, 2q) + [0, 2q).
+__device__ __forceinline__ u64 mul_shoup_approx(u64 b, u64 w, u64 ws, u64 q) {
+    const u32 b0 = (u32)b, b1 = (u32)(b >> 32), s0 = (u32)ws, s1 = (u32)(ws >> 32);
+    const u64 qe = (u64)b1 * s1 + __umulhi(b0, s1) + __umulhi(b1, s0);
+    return b * w - qe * q;
+}
 
 template <bool GROW>
 __device__ __forceinline__ void ct(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
     if constexpr (GROW) {
         u64 w, ws;
         tw_at(tab, idx, w, ws);
-        const u64 v = mul_shoup_lazy(b, w, ws, q);
-        b = a - v + 2 * q;
+        const u64 v = mul_shoup_approx(b, w, ws, q);  // [0, 4q)
+        b = a - v + 4 * q;
         a = a + v;
     } else {
         ct_bfly(a, b, tab, idx, q);
@@ -284,8 +296,8 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
 #pragma unroll
         for (int v = 0; v < 16; v++) x[v] = J.src[(size_t)(u + TPL * v) * C + col];
     }
-    // words enter below 4q; they leave below 4q (reducing) or 20q (growing: +2q per stage),
-    // and the row pass ends below 36q < 2^64 (q < 2^58)
+    // words enter below 4q; they leave below 4q (reducing) or 36q (growing: +4q per stage),
+    // and the row pass ends below 68q < 2^64 (q < 2^57)
     if (q < FWD_GROW_MAX) fwd_cols_stages<LOGS, true>(x, sm, u, c, tw, q);
     else fwd_cols_stages<LOGS, false>(x, sm, u, c, tw, q);
 #pragma unroll
@@ -350,7 +362,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__
         const u32 xi = u + TPL * v;
         const u64 y = sr[pad16(xi)];
         u64 val;
-        if (grow) {  // below 36q
+        if (grow) {  // below 68q
             val = red2(y, q, m.mu_hi);
             val = val >= q ? val - q : val;
         } else {  // below 4q
