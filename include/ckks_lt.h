@@ -38,6 +38,11 @@
  * ckks_last_error() gives a message for the calling thread.  Validation
  * failures return before any device work is queued.
  *
+ * Threads: evaluation calls (lt_eval*, the steps, the autotuners) on one
+ * context may run concurrently from several host threads, each on its own
+ * stream.  Uploading or replacing a key or diagonals, and destroying objects,
+ * must not overlap evaluation calls on the same context.
+ *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  * stream).  Calls that take a stream are asynchronous on it unless stated.
  * Device scratch memory is taken from the stream-ordered allocator of the
