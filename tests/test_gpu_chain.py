@@ -184,3 +184,18 @@ def test_recorded_chain_replays_on_new_inputs():
     with pytest.raises(binding.CkksError) as e:
         g.graph_begin(0)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("algo,split", [("th", (4, 4, 4)), ("dh", (8, 8)), ("bsgs", (8, 8))])
+def test_full_size_based_window_every_hoisting(algo, split):
+    """N = 2^16 at level 24: 64 diagonals at offsets -31*32 .. +32*32 (stride 32,
+    the middle stage of a radix-32 CoeffToSlot), bit-exact with the oracle for
+    TH-BSGS, DH-BSGS and BSGS."""
+    pb = make_problem("n16", 12, 64, stride=32, offset0=-992)
+    ensure_keys(pb, algo, split)
+    g = gpu_context("n16")
+    f = upload_problem(g, pb, stride=32)
+    out, _ = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, algo, split)
+    got = out.numpy()
+    assert_same(got, oracle_lt(pb, algo, split), f"n16 based {algo} {split}")
+    assert max_err(pb, got) <= 1e-4
