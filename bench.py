@@ -16,6 +16,9 @@ Prints one JSON line (rank 0):
              host memory and the result copied back inside each step
   roofline   the dominant kernel's algorithmic bytes / its live event-timed
              duration, against the measured HBM copy bandwidth
+  alu_roofline  per kernel class, its counted multiply-accumulates and NTT
+             butterflies at the rates of a live register-only probe of the
+             same arithmetic, over its measured time
   cpu_baseline  the CPU oracle timed on this host on one LT of the workload
 
 --impl reference times the CPU oracle alone (the reference arm).
@@ -205,6 +208,32 @@ def algorithmic_bytes_for(algo: str, cls: str, split, level: int, k: int, beta: 
             return rots * limb * (beta * ext + 2 * beta * ext + 2 * ext), rots
         return None, None
     return algorithmic_bytes(cls, split, level, k, beta, n_diag, N)
+
+
+def alu_roofline(binding, device: int, shares: dict, work: dict, dominant: str, dom_time: tuple,
+                 dom_work: tuple) -> dict:
+    """Integer-ALU roofline of every kernel class that does counted work:
+    frac = (its 128-bit multiply-accumulates at the probed MAC rate + its NTT
+    butterflies at the probed butterfly rate) / its measured device time.
+    The rates come from the library's register-only probe of the same
+    arithmetic, run here, after the timed region.  The dominant kernel uses
+    its timed-region launches, the others the warm-up launches."""
+    mac_rate, bfly_rate = binding.probe_int_rates(device)
+    kernels = {}
+    for c, (ms, n) in shares.items():
+        macs, bfly = work[c]
+        if c == dominant and dom_time[1]:
+            (ms, n), (macs, bfly) = dom_time, dom_work
+        if not n or not ms or (macs == 0 and bfly == 0):
+            continue
+        ideal_s = macs / mac_rate + bfly / bfly_rate
+        kernels[c] = {"macs_per_launch": int(macs / n), "butterflies_per_launch": int(bfly / n),
+                      "ms_per_launch": round(ms / n, 4), "frac": round(ideal_s / (ms / 1e3), 4)}
+    return {"bound": "alu", "unit": "fraction of the probed integer rate",
+            "peak": {"macs_per_s": round(mac_rate, -6), "butterflies_per_s": round(bfly_rate, -6)},
+            "peak_source": "register-only probe of the library's own 128-bit multiply-accumulate and growing "
+                           "NTT butterfly, run live on this GPU (ckks_probe_int_rates)",
+            "kernels": kernels}
 
 
 def lt_compulsory_bytes(split, level: int, k: int, beta: int, n_diag: int, N: int) -> int:
@@ -399,6 +428,7 @@ def run_ours(args, dist: Dist):
         g.lt_eval(ct, f, algo, split3, out=out)
     torch.cuda.synchronize()
     shares = {c: binding.profile_read(c) for c in binding.KERNEL_CLASSES}
+    work = {c: binding.profile_work(c) for c in binding.KERNEL_CLASSES}
     for c in binding.KERNEL_CLASSES:
         binding.profile_enable(c, False)
     tot = sum(v[0] for v in shares.values()) or 1.0
@@ -425,6 +455,7 @@ def run_ours(args, dist: Dist):
     dist.barrier()
     launches = binding.kernel_launches() - l0
     dom_ms, dom_n = binding.profile_read(dominant)
+    dom_work = binding.profile_work(dominant)
     binding.profile_enable(dominant, False)
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
@@ -482,6 +513,7 @@ def run_ours(args, dist: Dist):
             "compulsory_bytes": lt_bytes, "achieved_gbs": round(lt_bytes / (max_ms / args.steps / 1e3) / 1e9, 1),
             "frac": round(lt_bytes / (max_ms / args.steps / 1e3) / 1e9 / peak, 4)}),
         "roofline": roof,
+        "alu_roofline": alu_roofline(binding, dist.local, shares, work, dominant, (dom_ms, dom_n), dom_work),
         "kernel_shares": {c: round(v[0] / tot, 4) for c, v in shares.items()},
         "e2e": e2e,
         "gpu_launches": int(launches),

@@ -360,6 +360,27 @@ ckks_status ckks_profile_enable(const char* kernel_class, int on);
 ckks_status ckks_profile_read(const char* kernel_class, double* total_ms, uint64_t* launches);
 void ckks_profile_reset(void);
 
+/* Algorithmic integer work of the launches that ckks_profile_read times
+ * (same classes, same enable and reset), for the integer-ALU roofline:
+ * `macs` counts 128-bit multiply-accumulates of a residue by a residue
+ * ("diag_mac": two per diagonal product plus 2 beta per middle-layer step,
+ * Alg. 2 lines 8-14; "ks_inner": 2 beta per output word, the key inner
+ * product of Sec. II-A; "ntt_fwd_cols": the basis conversion of Eq. 3 fused
+ * into it, one per source limb and output word), `butterflies` counts NTT
+ * butterflies (N/2 per stage and limb, the stages of the pass).  EINVAL on
+ * an unknown name or a null output. */
+ckks_status ckks_profile_work(const char* kernel_class, double* macs, double* butterflies);
+
+/* Integer-rate probe, the denominator of that roofline: register-only loops
+ * of the library's own 128-bit multiply-accumulate and of its forward NTT
+ * butterfly (the growing Cooley-Tukey form of Sec. II-A's transform) on every
+ * SM of `device`, 8 CTAs of 256 threads per SM, best of two timed runs after
+ * a warm-up.  Returns multiply-accumulates and butterflies per second.
+ * Synchronous; allocates and frees a few KB of device memory and a stream of
+ * its own, so it must not be called while a stream of the device is being
+ * captured.  ECUDA on a CUDA error, EINVAL on a null output. */
+ckks_status ckks_probe_int_rates(int device, double* macs_per_s, double* butterflies_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -491,5 +491,27 @@ def profile_reset() -> None:
     lib().ckks_profile_reset()
 
 
+def profile_work(kernel_class: str):
+    """(128-bit multiply-accumulates, NTT butterflies) of the profiled launches
+    of a kernel class since the last reset."""
+    L = lib()
+    L.ckks_profile_work.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]
+    macs, bfly = ctypes.c_double(), ctypes.c_double()
+    check(L.ckks_profile_work(kernel_class.encode(), ctypes.byref(macs), ctypes.byref(bfly)))
+    return macs.value, bfly.value
+
+
+def probe_int_rates(device: int = 0):
+    """(multiply-accumulates per s, butterflies per s) of the library's own
+    arithmetic in register-only loops on `device`: the integer-ALU peaks."""
+    L = lib()
+    L.ckks_probe_int_rates.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+    macs, bfly = ctypes.c_double(), ctypes.c_double()
+    check(L.ckks_probe_int_rates(int(device), ctypes.byref(macs), ctypes.byref(bfly)))
+    return macs.value, bfly.value
+
+
 KERNEL_CLASSES = ["diag_mac", "ks_inner", "ntt_fwd_cols", "ntt_fwd_rows", "ntt_inv_rows", "ntt_inv_cols",
                   "automorphism", "add_gather"]

@@ -1027,6 +1027,24 @@ ckks_status ckks_profile_read(const char* kernel_class, double* total_ms, uint64
     });
 }
 
+ckks_status ckks_profile_work(const char* kernel_class, double* macs, double* butterflies) {
+    return guarded([&] {
+        const int c = prof_class(kernel_class);
+        if (c < 0 || !macs || !butterflies) fail(CKKS_EINVAL, "unknown kernel class or null output");
+        prof_work(c, macs, butterflies);
+    });
+}
+
+ckks_status ckks_probe_int_rates(int device, double* macs_per_s, double* butterflies_per_s) {
+    return guarded([&] {
+        if (!macs_per_s || !butterflies_per_s) fail(CKKS_EINVAL, "null output");
+        CK(cudaSetDevice(device));
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+        CK(probe_int_rates((u32)sms * 8, macs_per_s, butterflies_per_s));
+    });
+}
+
 void ckks_profile_reset(void) { prof_reset(); }
 uint64_t ckks_kernel_launch_count(void) { return ckks::launches(); }
 size_t ckks_device_bytes_in_use(const ckks_ctx* ctx) { return ctx ? ctx->bytes : 0; }

@@ -163,17 +163,25 @@ void count_launch(int n = 1);
 enum KClass { K_DIAG_MAC = 0, K_KS_INNER, K_FWD_COLS, K_FWD_ROWS, K_INV_ROWS, K_INV_COLS, K_AUTO, K_ADD, K_NCLASS };
 extern const char* const kclass_names[K_NCLASS];
 bool prof_on(int cls);
-// Brackets one launch with events when its class is enabled.
+// Brackets one launch with events when its class is enabled, and adds the
+// launch's algorithmic integer work (128-bit multiply-accumulates, NTT
+// butterflies) to the class's totals.
 struct ProfScope {
     int cls;
     cudaStream_t st;
     void* ev;
-    ProfScope(int c, cudaStream_t s);
+    ProfScope(int c, cudaStream_t s, double macs = 0, double butterflies = 0);
     ~ProfScope();
 };
 int prof_class(const char* name);
 void prof_enable(int cls, bool on);
 bool prof_read(int cls, double* ms, uint64_t* n);
+bool prof_work(int cls, double* macs, double* butterflies);
 void prof_reset();
+
+// Register-only rate probes of the library's own 128-bit multiply-accumulate
+// and forward NTT butterfly over `blocks` CTAs (best of two timed runs after a
+// warm-up); synchronous, on a stream of its own.
+cudaError_t probe_int_rates(u32 blocks, double* macs_per_s, double* butterflies_per_s);
 
 }  // namespace ckks

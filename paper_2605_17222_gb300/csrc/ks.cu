@@ -564,21 +564,21 @@ void launch_wait_selftest(u32* err, u64 limit_ns, cudaStream_t st) {
 
 void launch_ks_batch(const KsBatchArgs& a, cudaStream_t st) {
     const u32 N = 1u << a.log_n;
-    ProfScope ps(K_KS_INNER, st);
+    ProfScope ps(K_KS_INNER, st, 2.0 * a.beta * a.count * a.ext * N);
     k_ks_batch<<<dim3(((N + THREADS - 1) / THREADS) * a.count, a.ext), THREADS, 0, st>>>(a);
     count_launch();
 }
 
 void launch_ks_multi(const KsMultiArgs& a, cudaStream_t st) {
     const u32 N = 1u << a.log_n;
-    ProfScope ps(K_KS_INNER, st);
+    ProfScope ps(K_KS_INNER, st, 2.0 * a.beta * a.count * a.ext * N);
     k_ks_multi<<<dim3((N + THREADS - 1) / THREADS, a.ext), THREADS, 0, st>>>(a);
     count_launch();
 }
 
 void launch_ks_inner(const KsArgs& a, cudaStream_t st) {
     const u32 N = 1u << a.log_n;
-    ProfScope ps(K_KS_INNER, st);
+    ProfScope ps(K_KS_INNER, st, 2.0 * a.beta * a.ext * N);
     k_ks_inner<<<dim3((N + THREADS - 1) / THREADS, a.ext), THREADS, 0, st>>>(a);
     count_launch();
 }
@@ -588,7 +588,12 @@ void launch_diag_mac(const DiagMacArgs& a, cudaStream_t st) {
     u32 k3 = 1;
     while (k3 < a.n3 && k3 < (u32)DM_MAX_K3) k3 *= 2;
     const dim3 grid(((N + THREADS - 1) / THREADS) * a.batch, a.ext, (a.n3 + k3 - 1) / k3);
-    ProfScope ps(K_DIAG_MAC, st);
+    // multiply-accumulates: two per diagonal product (c0, c1), and the middle
+    // layer's 2 beta per step with j > 0, once per block of k3 outer indices
+    const double n1n2 = (double)a.n1 * a.n2, beta_mid = a.n2 > 1 ? a.beta : 0;
+    const double macs = (double)N * a.batch * a.ext *
+                        (2.0 * n1n2 * a.n3 + 2.0 * beta_mid * grid.z * (n1n2 - a.n1));
+    ProfScope ps(K_DIAG_MAC, st, macs);
     bool done = false;
     switch (k3) {
         case 1: done = launch_staged<1>(a, st); break;

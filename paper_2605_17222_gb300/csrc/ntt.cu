@@ -45,6 +45,8 @@ struct Profiler {
     std::vector<EvPair> pool;
     double ms[K_NCLASS] = {};
     uint64_t n[K_NCLASS] = {};
+    double mac[K_NCLASS] = {};   // algorithmic 128-bit multiply-accumulates of the timed launches
+    double bfly[K_NCLASS] = {};  // algorithmic NTT butterflies of the timed launches
     Profiler() {
         for (auto& o : on) o = false;
     }
@@ -93,6 +95,13 @@ bool prof_read(int cls, double* ms, uint64_t* n) {
     *n = P.n[cls];
     return true;
 }
+bool prof_work(int cls, double* macs, double* butterflies) {
+    Profiler& P = prof();
+    std::lock_guard<std::mutex> g(P.mu);
+    *macs = P.mac[cls];
+    *butterflies = P.bfly[cls];
+    return true;
+}
 void prof_reset() {
     Profiler& P = prof();
     std::lock_guard<std::mutex> g(P.mu);
@@ -100,10 +109,18 @@ void prof_reset() {
         P.drain(c);
         P.ms[c] = 0;
         P.n[c] = 0;
+        P.mac[c] = 0;
+        P.bfly[c] = 0;
     }
 }
-ProfScope::ProfScope(int c, cudaStream_t s) : cls(c), st(s), ev(nullptr) {
+ProfScope::ProfScope(int c, cudaStream_t s, double macs, double butterflies) : cls(c), st(s), ev(nullptr) {
     if (!prof_on(c)) return;
+    {
+        Profiler& P = prof();
+        std::lock_guard<std::mutex> g(P.mu);
+        P.mac[c] += macs;
+        P.bfly[c] += butterflies;
+    }
     EvPair* e = new EvPair(prof().get());
     cudaEventRecord(e->a, s);
     ev = e;
@@ -531,13 +548,17 @@ template <int LR, int LC>
 void fwd_impl(const NttTables& T, const Jobs<FwdJob>& p, int n, bool bconv, bool submul, cudaStream_t st) {
     const u32 N = 1u << T.log_n;
     const dim3 g1((N >> LR) / (THREADS / ((1u << LR) / 16)), n), g2((N >> LC) / (THREADS / ((1u << LC) / 16)), n);
+    const double half = (double)n * (N / 2);  // butterflies per stage over the launch's limbs
+    double bconv_macs = 0;
+    if (bconv)
+        for (int i = 0; i < n; i++) bconv_macs += (double)p.j[i].nsrc * N;
     {
-        ProfScope ps(K_FWD_COLS, st);
+        ProfScope ps(K_FWD_COLS, st, bconv_macs, half * LR);
         if (bconv) k_fwd_cols<LR, true><<<g1, THREADS, 0, st>>>(T, p);
         else k_fwd_cols<LR, false><<<g1, THREADS, 0, st>>>(T, p);
     }
     {
-        ProfScope ps(K_FWD_ROWS, st);
+        ProfScope ps(K_FWD_ROWS, st, 0, half * LC);
         if (submul) k_fwd_rows<LC, true><<<g2, THREADS, 0, st>>>(T, p);
         else k_fwd_rows<LC, false><<<g2, THREADS, 0, st>>>(T, p);
     }
@@ -547,13 +568,14 @@ template <int LR, int LC>
 void inv_impl(const NttTables& T, const Jobs<InvJob>& p, int n, bool gather, cudaStream_t st) {
     const u32 N = 1u << T.log_n;
     const dim3 g1((N >> LR) / (THREADS / ((1u << LR) / 16)), n), g2((N >> LC) / (THREADS / ((1u << LC) / 16)), n);
+    const double half = (double)n * (N / 2);
     {
-        ProfScope ps(K_INV_ROWS, st);
+        ProfScope ps(K_INV_ROWS, st, 0, half * LC);
         if (gather) k_inv_rows<LC, true><<<g2, THREADS, 0, st>>>(T, p);
         else k_inv_rows<LC, false><<<g2, THREADS, 0, st>>>(T, p);
     }
     {
-        ProfScope ps(K_INV_COLS, st);
+        ProfScope ps(K_INV_COLS, st, 0, half * LR);
         k_inv_cols<LR><<<g1, THREADS, 0, st>>>(T, p);
     }
 }
@@ -567,6 +589,58 @@ void inv_impl(const NttTables& T, const Jobs<InvJob>& p, int n, bool gather, cud
         case 15: IMPL<8, 7>(T, p, n, __VA_ARGS__, st); break;    \
         default: IMPL<8, 8>(T, p, n, __VA_ARGS__, st); break;    \
     }
+
+// ------------------------------------------------------------------ integer-rate probes
+// Register-only loops of the library's own arithmetic, the denominators of
+// the integer-ALU roofline: k_probe_mac runs mac128 into 8 independent
+// accumulators per thread, k_probe_bfly runs radix-16 rounds (4 stages of 8
+// growing forward butterflies, ct<true>) on 16 words per thread with the 15
+// twiddles of a round held in registers.  Each thread writes one word so that
+// nothing is optimised away; the values themselves are meaningless.
+constexpr int PROBE_ITERS = 1024, PROBE_THREADS = 256, PROBE_MACS = 8;
+
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_mac(const u64* __restrict__ in, u64* __restrict__ out) {
+    const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
+    u64 b[PROBE_MACS];
+    U128 acc[PROBE_MACS];
+#pragma unroll
+    for (int k = 0; k < PROBE_MACS; k++) {
+        b[k] = in[(tid + k) & 1023];
+        acc[k] = U128{0, 0};
+    }
+    u64 x = in[tid & 1023];
+    for (int i = 0; i < PROBE_ITERS; i++) {
+        x ^= (u64)i;
+#pragma unroll
+        for (int k = 0; k < PROBE_MACS; k++) mac128(acc[k], x, b[k]);
+    }
+    u64 r = 0;
+#pragma unroll
+    for (int k = 0; k < PROBE_MACS; k++) r ^= acc[k].lo ^ acc[k].hi;
+    out[tid] = r;
+}
+
+__global__ void __launch_bounds__(PROBE_THREADS, 4) k_probe_bfly(const ulonglong2* __restrict__ tw,
+                                                                 const u64* __restrict__ in, u64* __restrict__ out,
+                                                                 u64 q) {
+    const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
+    u64 x[16];
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = in[(tid * 16 + v) & 1023];
+    for (int i = 0; i < PROBE_ITERS; i++) {
+#pragma unroll
+        for (int ss = 0; ss < 4; ss++) {
+            const int tv = 8 >> ss;
+#pragma unroll
+            for (int v = 0; v < 16; v++)
+                if (!(v & tv)) ct<true>(x[v], x[v + tv], tw, (1u << ss) + (v >> (4 - ss)), q);
+        }
+    }
+    u64 r = 0;
+#pragma unroll
+    for (int v = 0; v < 16; v++) r ^= x[v] * (u64)(v + 1);
+    out[tid] = r;
+}
 
 }  // namespace
 
@@ -594,6 +668,60 @@ void launch_automorphism(const u64* in, u64* out, u32 n_limbs, u32 gal, u32 log_
     ProfScope ps(K_AUTO, st);
     k_automorphism<<<dim3((N + 255) / 256, n_limbs), 256, 0, st>>>(in, out, gal, log_n);
     count_launch();
+}
+
+cudaError_t probe_int_rates(u32 blocks, double* macs_per_s, double* butterflies_per_s) {
+    // q: any odd modulus below 2^57 (the growing butterflies' range); the
+    // twiddles are arbitrary residues with their Shoup companions
+    const u64 q = (1ull << 56) - 5;
+    u64 h_in[1024];
+    ulonglong2 h_tw[16];
+    for (int i = 0; i < 1024; i++) h_in[i] = (0x9E3779B97F4A7C15ull * (u64)(i + 1)) % q;
+    for (int i = 0; i < 16; i++) {
+        const u64 w = (0xD1B54A32D192ED03ull * (u64)(i + 3)) % q;
+        h_tw[i] = make_ulonglong2(w, (u64)(((unsigned __int128)w << 64) / q));
+    }
+    u64 *in = nullptr, *out = nullptr;
+    ulonglong2* tw = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err = cudaSuccess;
+    float best[2] = {0, 0};
+    auto step = [&](cudaError_t e) {
+        if (err == cudaSuccess) err = e;
+        return err == cudaSuccess;
+    };
+    if (step(cudaMalloc(&in, sizeof(h_in))) && step(cudaMalloc(&tw, sizeof(h_tw))) &&
+        step(cudaMalloc(&out, (size_t)blocks * PROBE_THREADS * sizeof(u64))) &&
+        step(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) && step(cudaEventCreate(&e0)) &&
+        step(cudaEventCreate(&e1)) && step(cudaMemcpyAsync(in, h_in, sizeof(h_in), cudaMemcpyHostToDevice, st)) &&
+        step(cudaMemcpyAsync(tw, h_tw, sizeof(h_tw), cudaMemcpyHostToDevice, st))) {
+        for (int which = 0; which < 2 && err == cudaSuccess; which++)
+            for (int rep = 0; rep < 3 && err == cudaSuccess; rep++) {  // the first run warms up
+                step(cudaEventRecord(e0, st));
+                if (which == 0) k_probe_mac<<<blocks, PROBE_THREADS, 0, st>>>(in, out);
+                else k_probe_bfly<<<blocks, PROBE_THREADS, 0, st>>>(tw, in, out, q);
+                count_launch();
+                step(cudaGetLastError());
+                step(cudaEventRecord(e1, st));
+                step(cudaEventSynchronize(e1));
+                float ms = 0;
+                if (step(cudaEventElapsedTime(&ms, e0, e1)) && rep > 0 && (best[which] == 0 || ms < best[which]))
+                    best[which] = ms;
+            }
+    }
+    if (st) cudaStreamSynchronize(st);
+    if (in) cudaFree(in);
+    if (tw) cudaFree(tw);
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (err != cudaSuccess) return err;
+    const double threads = (double)blocks * PROBE_THREADS;
+    *macs_per_s = threads * PROBE_ITERS * PROBE_MACS / (best[0] * 1e-3);
+    *butterflies_per_s = threads * PROBE_ITERS * 32 / (best[1] * 1e-3);
+    return cudaSuccess;
 }
 
 void launch_add_gather(const ModC* mods, const AddJob* jobs, int njobs, u32 gal, int accumulate, u32 log_n,
