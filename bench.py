@@ -594,6 +594,19 @@ def run_batched(args, dist: Dist):
     ms_seq = timed(sequential, steps)
     clk = clocks.stop()
     rec.close()
+    # integer-ALU roofline of one batch step, untimed: profiled lt_eval_batch (a graph replay makes no
+    # host launches to bracket); the lanes' kernels overlap, so a launch's event time includes time it
+    # shares with other lanes and the fractions are lower bounds
+    for c in binding.KERNEL_CLASSES:
+        binding.profile_enable(c, True)
+    binding.profile_reset()
+    g.lt_eval_batch(cts, [f] * n_ct, algos=["th"] * n_ct, splits=sp_list, outs=outs)
+    torch.cuda.synchronize()
+    shares_b = {c: binding.profile_read(c) for c in binding.KERNEL_CLASSES}
+    work_b = {c: binding.profile_work(c) for c in binding.KERNEL_CLASSES}
+    for c in binding.KERNEL_CLASSES:
+        binding.profile_enable(c, False)
+    alu = alu_roofline(binding, dist.local, shares_b, work_b, "", (0.0, 0), (0.0, 0.0))
     # compulsory bytes of one step: diagonals and keys once per level used, every ciphertext in and out
     limb = 8 * ps.n
     comp = 0
@@ -624,6 +637,7 @@ def run_batched(args, dist: Dist):
         "speedup_vs_sequential": round(ms_seq / ms_graph, 3),
         "hbm_roofline_batch": {"compulsory_bytes": comp,
                                "frac": round(comp / (ms_graph / steps / 1e3) / 1e9 / peak, 4)},
+        "alu_roofline_batch": alu,
         "clocks": clk,
     }
 
