@@ -137,9 +137,9 @@ struct ckks_ctx {
     DevBuf d_mods, d_psi, d_ipsi, d_lift, d_lift_sh, d_err;
     NttTables T{};
     std::map<u32, LevelConsts> levels;
-    std::map<u32, u64*> keys;  // rotation (mod N/2) -> [beta_max][2][L+K][N]
+    std::map<u32, u64*> keys;  // rotation (mod N/2) -> [beta_max][L+K][N] word pairs (components interleaved)
     std::map<std::tuple<int, u32, u32, int32_t, int32_t>, lt_split> tuned;  // (algo, level, D, stride, offset0 mod N/2)
-    std::mutex mu;
+    mutable std::mutex mu;
     size_t bytes = 0;
     // fork/join lanes of lt_eval_batch: independent groups run on the caller's
     // stream and up to FORK_LANES - 1 more, so that one group's NTT-bound
@@ -943,37 +943,12 @@ static lt_split choose_split(const ckks_ctx* C, lt_algo algo, u32 level, u32 D, 
                              int32_t offset0 = 0) {
     if (algo == LT_DIAG) return lt_split{1, D, 1};
     {
-        std::lock_guard<std::mutex> g(const_cast<ckks_ctx*>(C)->mu);
+        std::lock_guard<std::mutex> g(C->mu);
         auto it = C->tuned.find(std::make_tuple((int)algo, level, D, stride, (int32_t)C->rotkey(offset0)));
         if (it != C->tuned.end()) return it->second;
     }
     std::vector<lt_split> r = ranked_splits(C, algo, level, D);
     return r.empty() ? lt_split{0, 0, 0} : r[0];
-}
-
-[[maybe_unused]] static lt_split choose_split_model_only(const ckks_ctx* C, lt_algo algo, u32 level, u32 D) {
-    lt_split best{0, 0, 0};
-    if (algo == LT_DIAG) return lt_split{1, D, 1};
-    double bt = 1e300;
-    std::vector<u32> divs;
-    for (u32 d = 1; d <= D; d++)
-        if (D % d == 0) divs.push_back(d);
-    for (u32 a : divs)
-        for (u32 b : divs) {
-            if ((u64)a * b > D || D % ((u64)a * b)) continue;
-            lt_split sp;
-            if (algo == LT_TH_BSGS) {
-                sp = lt_split{a, b, D / (a * b)};
-                if (sp.n1 > (u32)DM_MAX_N1 || sp.n3 > (u32)DM_MAX_N3 || sp.n2 > (u32)DM_MAX_N2) continue;
-            } else {
-                if (a * b != D) continue;
-                sp = lt_split{a, b, 1};
-                if (sp.n1 > (u32)DM_MAX_N1 || sp.n2 > (u32)DM_MAX_N3) continue;
-            }
-            const double t = model_time(C, algo, level, D, sp);
-            if (t < bt) bt = t, best = sp;
-        }
-    return best;
 }
 
 // ------------------------------------------------------------------ C ABI

@@ -65,7 +65,7 @@ void launch_add_gather(const ModC* mods, const AddJob* jobs, int njobs, u32 gal,
 // Switching-key inner product with hoisted automorphism (K4).
 struct KsArgs {
     const u64* digits;      // [beta][ext][N]
-    const u64* key;         // [beta_max][2][L+k][N]
+    const u64* key;         // [beta_max][L+k][N] word pairs (interleaved layout below)
     const u64* x0;          // null, ext poly, or Q poly to lift
     u64* out0;
     u64* out1;
@@ -82,7 +82,7 @@ void launch_ks_inner(const KsArgs& a, cudaStream_t st);
 constexpr int KS_MAX_MULTI = 64;
 struct KsMultiArgs {
     const u64* digits[KS_MAX_MULTI];  // [beta][ext][N] each
-    const u64* keys[KS_MAX_MULTI];    // [beta_max][2][L+k][N] each
+    const u64* keys[KS_MAX_MULTI];    // [beta_max][L+k][N] word pairs each (interleaved)
     const u64* x0[KS_MAX_MULTI];      // [ext][N] each
     u32 gal[KS_MAX_MULTI];
     u64* out0;

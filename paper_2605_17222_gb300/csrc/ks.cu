@@ -15,6 +15,8 @@
 // reduced once (PE modes CWPM-ACC / CM-ACC of Sec. V, done lazily).
 #include "kernels.h"
 
+#include <atomic>
+
 namespace ckks {
 namespace {
 
@@ -524,11 +526,27 @@ bool try_staged(const DiagMacArgs& a, cudaStream_t st) {
     const size_t sm = 8ull * RUN * NS * (K3 + beta + 2) + ((4ull * a.n2 + 15) & ~15ull);  // stages + srun table
     const u32 N = 1u << a.log_n;
     if (sm > DM_SMEM_MAX || N % RUN || beta > (size_t)KB) return false;
-    static int attr_ok = -1;
-    if (attr_ok < 0)
-        attr_ok = cudaFuncSetAttribute(k_diag_mac_staged<K3, RUN, NS, KB>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DM_SMEM_MAX) == cudaSuccess;
-    if (!attr_ok) return false;
+    // The dynamic shared-memory limit is a per-device function attribute: set
+    // it once per device (threads may race to set it; the call is idempotent).
+    // A device that refuses it falls back to the next variant, and the error
+    // the refusal left is cleared so that a later status check does not see it.
+    static std::atomic<uint64_t> attr_set{0}, attr_bad{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return false;
+    }
+    const uint64_t bit = 1ull << dev;
+    if (attr_bad.load(std::memory_order_relaxed) & bit) return false;
+    if (!(attr_set.load(std::memory_order_acquire) & bit)) {
+        if (cudaFuncSetAttribute(k_diag_mac_staged<K3, RUN, NS, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)DM_SMEM_MAX) != cudaSuccess) {
+            cudaGetLastError();
+            attr_bad.fetch_or(bit, std::memory_order_relaxed);
+            return false;
+        }
+        attr_set.fetch_or(bit, std::memory_order_release);
+    }
     const dim3 grid((N / RUN) * a.batch, a.ext, (a.n3 + K3 - 1) / K3);
     k_diag_mac_staged<K3, RUN, NS, KB><<<grid, RUN, sm, st>>>(a);
     return true;
