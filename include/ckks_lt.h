@@ -40,8 +40,9 @@
  *
  * Threads: evaluation calls (lt_eval*, the steps, the autotuners) on one
  * context may run concurrently from several host threads, each on its own
- * stream.  Uploading or replacing a key or diagonals, and destroying objects,
- * must not overlap evaluation calls on the same context.
+ * stream.  Creating, uploading or replacing keys, diagonals and ciphertexts,
+ * and destroying objects, change the context's tables: such calls must not
+ * overlap each other or evaluation calls on the same context.
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  * stream).  Calls that take a stream are asynchronous on it unless stated.
