@@ -40,9 +40,12 @@
  *
  * Threads: evaluation calls (lt_eval*, the steps, the autotuners) on one
  * context may run concurrently from several host threads, each on its own
- * stream.  Creating, uploading or replacing keys, diagonals and ciphertexts,
- * and destroying objects, change the context's tables: such calls must not
- * overlap each other or evaluation calls on the same context.
+ * stream.  Uploading or replacing keys and diagonals, allocating
+ * library-owned ciphertexts (ckks_ct_create, ckks_ct_upload) and destroying
+ * objects update the context's tables and memory count: such calls must not
+ * overlap each other or evaluation calls on the same context.  Wrapping
+ * caller memory (ckks_ct_wrap_device) and freeing a wrapped handle may run at
+ * any time.
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  * stream).  Calls that take a stream are asynchronous on it unless stated.
