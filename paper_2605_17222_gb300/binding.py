@@ -92,6 +92,10 @@ def lib():
         "lt_graph_end": [P, P, PP],
         "lt_graph_destroy": [P],
         "ckks_selftest_bounded_wait": [P, U32, P],
+        "ckks_profile_enable": [ctypes.c_char_p, I],
+        "ckks_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
+        "ckks_profile_work": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+        "ckks_probe_int_rates": [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -109,6 +113,9 @@ def lib():
     L.ckks_ct_level.restype = U32
     L.ckks_ct_device_ptr.argtypes = [P]
     L.ckks_ct_device_ptr.restype = P
+    L.lt_candidate_splits.argtypes = [P, I, U32, U32, P, U32]
+    L.lt_candidate_splits.restype = I32
+    L.ckks_profile_reset.restype = None
     _lib = L
     return L
 
@@ -318,12 +325,8 @@ class Context:
 
     def candidate_splits(self, algo: str, level: int, n_diag: int, count: int):
         """The cost model's `count` best splits, fastest first (lt_candidate_splits)."""
-        L = lib()
-        L.lt_candidate_splits.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
-                                          ctypes.c_void_p, ctypes.c_uint32]
-        L.lt_candidate_splits.restype = ctypes.c_int32
         buf = (Split * count)()
-        n = L.lt_candidate_splits(self.h, ALGOS[algo], level, n_diag, buf, count)
+        n = lib().lt_candidate_splits(self.h, ALGOS[algo], level, n_diag, buf, count)
         if n < 0:
             raise CkksError(1, "bad arguments")
         return [buf[i].tuple() for i in range(n)]
@@ -472,18 +475,13 @@ def kernel_launches() -> int:
 
 
 def profile_enable(kernel_class: str, on: bool = True) -> None:
-    L = lib()
-    L.ckks_profile_enable.argtypes = [ctypes.c_char_p, ctypes.c_int]
-    check(L.ckks_profile_enable(kernel_class.encode(), int(on)))
+    check(lib().ckks_profile_enable(kernel_class.encode(), int(on)))
 
 
 def profile_read(kernel_class: str):
     """(total device ms, launches) of a kernel class since the last reset."""
-    L = lib()
-    L.ckks_profile_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
-                                    ctypes.POINTER(ctypes.c_uint64)]
     ms, n = ctypes.c_double(), ctypes.c_uint64()
-    check(L.ckks_profile_read(kernel_class.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    check(lib().ckks_profile_read(kernel_class.encode(), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
 
 
@@ -494,22 +492,16 @@ def profile_reset() -> None:
 def profile_work(kernel_class: str):
     """(128-bit multiply-accumulates, NTT butterflies) of the profiled launches
     of a kernel class since the last reset."""
-    L = lib()
-    L.ckks_profile_work.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
-                                    ctypes.POINTER(ctypes.c_double)]
     macs, bfly = ctypes.c_double(), ctypes.c_double()
-    check(L.ckks_profile_work(kernel_class.encode(), ctypes.byref(macs), ctypes.byref(bfly)))
+    check(lib().ckks_profile_work(kernel_class.encode(), ctypes.byref(macs), ctypes.byref(bfly)))
     return macs.value, bfly.value
 
 
 def probe_int_rates(device: int = 0):
     """(multiply-accumulates per s, butterflies per s) of the library's own
     arithmetic in register-only loops on `device`: the integer-ALU peaks."""
-    L = lib()
-    L.ckks_probe_int_rates.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                                       ctypes.POINTER(ctypes.c_double)]
     macs, bfly = ctypes.c_double(), ctypes.c_double()
-    check(L.ckks_probe_int_rates(int(device), ctypes.byref(macs), ctypes.byref(bfly)))
+    check(lib().ckks_probe_int_rates(int(device), ctypes.byref(macs), ctypes.byref(bfly)))
     return macs.value, bfly.value
 
 

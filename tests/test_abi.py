@@ -34,3 +34,26 @@ def test_errors_without_device_are_reported():
     st = L.ckks_ctx_create(None, 12, None, 0, None, 0, 1, 0)
     assert st == 1
     assert b"null" in L.ckks_last_error()
+
+
+def test_profile_calls_without_device():
+    """The live-timing and work counters are host bookkeeping: every class reads
+    zero after a reset, enabling launches nothing, and an unknown class or a
+    null output is rejected with CKKS_EINVAL."""
+    binding.profile_reset()
+    for c in binding.KERNEL_CLASSES:
+        binding.profile_enable(c, True)
+        assert binding.profile_read(c) == (0.0, 0)
+        assert binding.profile_work(c) == (0.0, 0.0)
+        binding.profile_enable(c, False)
+    for call in (lambda: binding.profile_read("no_such_kernel"), lambda: binding.profile_work("no_such_kernel"),
+                 lambda: binding.profile_enable("no_such_kernel")):
+        try:
+            call()
+        except binding.CkksError as e:
+            assert e.status == 1
+        else:
+            raise AssertionError("unknown kernel class accepted")
+    L = binding.lib()
+    assert L.ckks_profile_work(b"diag_mac", None, None) == 1
+    assert L.ckks_probe_int_rates(0, None, None) == 1
