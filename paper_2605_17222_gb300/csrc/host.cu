@@ -212,6 +212,19 @@ const LevelConsts& ckks_ctx::lc(u32 level) {
     if (it != levels.end()) return it->second;
     LevelConsts c;
     const u32 ext = level + K, beta = this->beta(level);
+    // the device tables uploaded so far are freed (and uncounted) if a later upload fails
+    struct Unwind {
+        ckks_ctx* ctx;
+        LevelConsts* c;
+        size_t words[4];
+        bool armed = true;
+        ~Unwind() {
+            if (!armed) return;
+            u64* tabs[4] = {c->dec_tab, c->md_tab, c->mdr_tab, c->rs_tab};
+            for (int i = 0; i < 4; i++) ctx->dfree(tabs[i], words[i]);
+        }
+    } unwind{this, &c, {(size_t)beta * ext * alpha, (size_t)level * K, (size_t)(level - 1) * (K + 1),
+                        (size_t)(level - 1)}};
     auto modof = [&](u32 t) { return mods[gmod(level, t)]; };
     // Decompose, Eq. (3) per digit
     c.dec_c.resize(level);
@@ -281,6 +294,7 @@ const LevelConsts& ckks_ctx::lc(u32 level) {
         down(S, level - 1, c.mdr_c, c.mdr_sh, c.mdr_pinv, c.mdr_pinv_sh, c.mdr_tab);
         down(std::vector<u32>{level - 1}, level - 1, c.rs_c, c.rs_sh, c.rs_inv, c.rs_inv_sh, c.rs_tab);
     }
+    unwind.armed = false;
     return levels.emplace(level, std::move(c)).first->second;
 }
 
