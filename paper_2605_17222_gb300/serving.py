@@ -162,14 +162,16 @@ class LtServer:
             ev = torch.cuda.Event()
             ev.record(stream)
         nbytes = sum(r.scratch_bytes for r in batch)
-        self.inflight[si] = (ev, batch, nbytes)
-        self.inflight_bytes += nbytes
-        self.stats.max_inflight_bytes = max(self.stats.max_inflight_bytes, self.inflight_bytes)
-        self.stats.batches += 1
+        with self.lock:  # pending() may read the in-flight table from a submitting thread
+            self.inflight[si] = (ev, batch, nbytes)
+            self.inflight_bytes += nbytes
+            self.stats.max_inflight_bytes = max(self.stats.max_inflight_bytes, self.inflight_bytes)
+            self.stats.batches += 1
 
     def _retire(self) -> None:
-        for si in list(self.inflight):
-            ev, batch, nbytes = self.inflight[si]
+        with self.lock:
+            items = list(self.inflight.items())
+        for si, (ev, batch, nbytes) in items:
             if ev.query():
                 now = time.perf_counter()
                 for r in batch:
@@ -177,8 +179,9 @@ class LtServer:
                     self.stats.latencies.append(now - r.arrival)
                     self.completed.append(r)
                 self.stats.completed += len(batch)
-                self.inflight_bytes -= nbytes
-                del self.inflight[si]
+                with self.lock:
+                    self.inflight_bytes -= nbytes
+                    del self.inflight[si]
 
 
 def percentile(xs, p: float) -> float:

@@ -59,3 +59,45 @@ def test_percentile():
     xs = list(range(1, 101))
     assert percentile(xs, 50) in (50, 51)
     assert percentile(xs, 99) == 99
+
+
+def test_retire_while_another_thread_counts_pending():
+    """Batches retire (their completion events fire) while a submitting thread
+    keeps reading pending(): the in-flight table is only changed under the
+    server's lock, so the reader never sees it mid-update, and every request,
+    byte and batch is accounted for once."""
+    import threading
+
+    class Ev:
+        def __init__(self, polls):
+            self.polls = polls
+
+        def query(self):
+            self.polls -= 1
+            return self.polls <= 0
+
+    srv = LtServer({"a": FakeCtx()}, hbm_budget=1e12, resident_bytes=0, streams=64)
+    for si in range(64):
+        srv.inflight[si] = (Ev(1 + si % 5), [_req(si, "a", 3, t=0.0)], 100)
+        srv.inflight_bytes += 100
+    errors, seen = [], []
+    stop = threading.Event()
+
+    def reader():
+        while not stop.is_set():
+            try:
+                seen.append(srv.pending())
+            except Exception as e:  # a dict mutated during iteration would land here
+                errors.append(e)
+                return
+
+    t = threading.Thread(target=reader)
+    t.start()
+    for _ in range(10):
+        srv._retire()
+    stop.set()
+    t.join()
+    assert not errors
+    assert srv.inflight == {} and srv.inflight_bytes == 0
+    assert srv.stats.completed == 64 and sorted(r.rid for r in srv.completed) == list(range(64))
+    assert all(0 <= n <= 64 for n in seen)
