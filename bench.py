@@ -48,22 +48,27 @@ SEED = 1
 
 
 def parse():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="th", choices=["th", "dh", "bsgs", "diag"])
+    ap = argparse.ArgumentParser(description="Throughput of the CKKS linear transformation; prints one JSON line.")
+    ap.add_argument("--gpus", type=int, default=1, help="GPUs (one rank each under torchrun; replicas, weak scaling)")
+    ap.add_argument("--steps", type=int, default=200, help="timed steps")
+    ap.add_argument("--warmup", type=int, default=5, help="untimed warm-up steps (at least 3 are run)")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"],
+                    help="reference: the CPU oracle on this host's cores")
+    ap.add_argument("--algo", default="th", choices=["th", "dh", "bsgs", "diag"],
+                    help="TH-BSGS (Alg. 2), DH-BSGS (Alg. 1), BSGS (Eq. 5) or the diagonal method")
     ap.add_argument("--split", default="", help="e.g. 4,8,8 (default: the library's choice)")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip timing the CPU oracle")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run with host copies")
     ap.add_argument("--diags", type=int, default=256, help="number of diagonals (256 = the benchmark workload)")
     ap.add_argument("--level", type=int, default=24, help="ciphertext level (24 = the benchmark workload)")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batched", "uneven", "serving", "paper-a", "paper-b", "cts", "stc", "steps"],
                     help="single: one LT per step (the headline); batched: 64 ciphertexts at levels "
-                         "{8,16,24} and one shared 256-diagonal matrix per step; serving: Poisson "
-                         "arrivals of LT requests through the continuous-batching server")
+                         "{8,16,24} and one shared 256-diagonal matrix per step; uneven: 128 LTs over 20 "
+                         "(diagonals, stride) shapes per step; serving: Poisson arrivals of LT requests "
+                         "through the continuous-batching server; paper-a / paper-b: the paper's Set-A / "
+                         "Set-B dense LTs; cts / stc: CoeffToSlot / SlotToCoeff chains at N=2^16; steps: "
+                         "the key-switching steps one at a time")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: requests per second")
     return ap.parse_args()
