@@ -173,10 +173,13 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- byte model
 def algorithmic_bytes(cls: str, split, level: int, k: int, beta: int, n_diag: int, N: int,
                       outer_rotated: int | None = None) -> tuple:
-    """(bytes, launches) per LT of one kernel class in the TH/DH schedule:
-    the words the step must read and write once (keys, diagonals, digits,
-    inputs, outputs), 8 bytes each.  outer_rotated: how many outer amounts are
-    nonzero (n3 - 1 for consecutive offsets from 0; up to n3 with a base)."""
+    """(bytes, launches) per LT of one kernel class in the TH/DH schedule: the
+    compulsory words the class must read, 8 bytes each -- the diagonals and
+    the switching keys it streams (the per-LT byte formula's D (l+k) and
+    K 2 beta (l+k) terms).  Intermediates (digits, baby pairs, partial sums)
+    are not algorithmic bytes; the ncu traffic shows what they add.
+    outer_rotated: how many outer amounts are nonzero (n3 - 1 for consecutive
+    offsets from 0; up to n3 with a base)."""
     n1, n2, n3 = split
     n_out = n3 - 1 if outer_rotated is None else outer_rotated
     ext = level + k
@@ -184,14 +187,9 @@ def algorithmic_bytes(cls: str, split, level: int, k: int, beta: int, n_diag: in
     if cls == "diag_mac":
         limbs = n_diag * ext                                   # diagonals
         limbs += (n2 - 1) * 2 * beta * ext                      # middle-layer keys
-        limbs += (n1 * beta * ext) if n2 > 1 else 0             # digits of each baby index
-        limbs += 2 * (n1 - 1) * ext + 2 * level                 # baby pairs (A_i, B_i) and the input ciphertext
-        limbs += 2 * n3 * ext                                   # outputs u_k
         return limbs * limb, 1
     if cls == "ks_inner":
-        p1 = (n1 - 1) * (beta * ext + 2 * beta * ext + level + 2 * ext)
-        p5 = n_out * (beta * ext + 2 * beta * ext + ext + 4 * ext)
-        return (p1 + p5) * limb, (n1 - 1) + n_out
+        return ((n1 - 1) + n_out) * 2 * beta * ext * limb, (n1 - 1) + n_out   # inner- and outer-layer keys
     return None, None
 
 
@@ -207,10 +205,10 @@ def algorithmic_bytes_for(algo: str, cls: str, split, level: int, k: int, beta: 
         n1, n2 = split[0], split[1]
         limb, ext = 8 * N, level + k
         if cls == "diag_mac":
-            return limb * (n_diag * level + 2 * n1 * level + 2 * n2 * level), 1
+            return limb * n_diag * level, 1
         if cls == "ks_inner":
             rots = (n1 - 1) + (n2 - 1)
-            return rots * limb * (beta * ext + 2 * beta * ext + 2 * ext), rots
+            return rots * limb * 2 * beta * ext, rots
         return None, None
     return algorithmic_bytes(cls, split, level, k, beta, n_diag, N)
 
@@ -295,7 +293,7 @@ def time_oracle(ps, algo, split, keys, diags, ct, budget_s: float, max_steps: in
                 warmup_budget_s: float = 0.0):
     """Times full oracle LTs until `max_steps` or `budget_s` (at least one),
     after up to `warmup` untimed LTs that stop early once `warmup_budget_s` is
-    spent.  Returns (times, warm-up LTs run)."""
+    spent.  Returns (times, warm-up LTs run, the last LT's output [2][level-1][N])."""
     from oracle import lt as olt
     from oracle.ckks import Ctx
     octx = Ctx(ps)
@@ -303,15 +301,29 @@ def time_oracle(ps, algo, split, keys, diags, ct, budget_s: float, max_steps: in
     while warm < warmup and (warm == 0 or time.perf_counter() - w_start < warmup_budget_s):
         olt.run(octx, algo, ct, diags, keys, split if algo != "diag" else None)
         warm += 1
-    times = []
+    times, out = [], None
     t_start = time.perf_counter()
     while len(times) < max(1, max_steps):
         t0 = time.perf_counter()
-        olt.run(octx, algo, ct, diags, keys, split if algo != "diag" else None)
+        out, _ = olt.run(octx, algo, ct, diags, keys, split if algo != "diag" else None)
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_start + times[-1] > budget_s:
             break
-    return times, warm
+    return times, warm, out
+
+
+def parity_with_oracle(got, want) -> dict:
+    """Word-for-word comparison of the GPU's output residues with the oracle's."""
+    import numpy as np
+    want = np.stack(want)
+    if got.shape != want.shape:
+        return {"parity": "mismatch", "detail": f"shape {list(got.shape)} vs {list(want.shape)}"}
+    diff = np.argwhere(got != want)
+    if diff.size == 0:
+        return {"parity": "bit-exact", "words": int(got.size)}
+    i = tuple(int(v) for v in diff[0])
+    return {"parity": "mismatch", "words": int(got.size), "differing": int(len(diff)), "first_index": list(i),
+            "gpu": int(got[i]), "oracle": int(want[i])}
 
 
 def cores_used() -> int:
@@ -527,7 +539,11 @@ def run_ours(args, dist: Dist):
     # ---------------------------------------------------------------- CPU oracle baseline
     if not args.no_cpu_baseline and dist.rank == 0 and dist.world == 1:
         keys, diags, cth = oracle_problem_from_device(ps, g, split3, keys_t, diags_t, ct_t)
-        times, _ = time_oracle(ps, algo, split3, keys, diags, cth, budget_s=30.0, max_steps=1)
+        times, _, want = time_oracle(ps, algo, split3, keys, diags, cth, budget_s=30.0, max_steps=1)
+        # the timed split's GPU output (every timed LT wrote the same residues into `out`)
+        # against the oracle's on the same inputs
+        result["parity"] = dict(parity_with_oracle(out.numpy(), want),
+                                against=f"CPU oracle, same inputs and split {list(split3)}")
         result["cpu_baseline"] = {
             "value": round(len(times) / sum(times), 5), "unit": "LT/s", "cores": cores_used(), "kind": "oracle",
             "sample": f"{len(times)} full LT(s) of this workload ({algo}, split {list(split3)}) on the same "
@@ -1180,7 +1196,7 @@ def run_reference(args, dist: Dist):
     diags = np.stack([synth.uniform_mod(SEED, f"diag/{t}", top, N) for t in range(D)])
     ct = (synth.uniform_mod(SEED, "ct0", ps.q[:LEVEL], N), synth.uniform_mod(SEED, "ct1", ps.q[:LEVEL], N))
     budget, warm_budget = 150.0, 40.0
-    times, warm = time_oracle(ps, args.algo, split3, keys, diags, ct, budget_s=budget, max_steps=args.steps,
+    times, warm, _ = time_oracle(ps, args.algo, split3, keys, diags, ct, budget_s=budget, max_steps=args.steps,
                               warmup=args.warmup, warmup_budget_s=warm_budget)
     total = sum(times)
     v = len(times) / total

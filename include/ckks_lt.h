@@ -306,9 +306,12 @@ ckks_status ckks_moddown(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint6
 ckks_status ckks_moddown_rescale(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint64_t* out,
                                  void* stream);
 
-/* ModDown exactly as ckks_moddown, for callers that must not allocate device
- * memory while they run (code recorded into a CUDA graph, code under an
- * external memory budget or allocator, paths where cudaMalloc is off limits).
+/* ModDown exactly as ckks_moddown, for host programs that cannot let the
+ * library allocate device memory while it runs: an application that owns
+ * every byte of the GPU through its own allocator or memory budget (a
+ * library-side cudaMalloc would take memory outside that budget), or a
+ * latency-bound path where a cudaMalloc and the device synchronisation it
+ * may imply are not acceptable.  The caller passes x and out.
  * The paper has no counterpart: this is a deployment variant.  Its scratch is
  * a fixed device array inside the library of 8 limbs at N = 2^16 (4 MiB,
  * k * N <= 524288 words); every GPU that loads the library holds it until
@@ -346,6 +349,19 @@ ckks_status ckks_device_status(ckks_ctx* ctx);
  * (1..5000) milliseconds.  The next ckks_device_status then reports
  * CKKS_ETIMEOUT and the context stays usable.  Faults nothing. */
 ckks_status ckks_selftest_bounded_wait(ckks_ctx* ctx, uint32_t limit_ms, void* stream);
+
+/* Failure-detection test hook of the TMA-staged diagonal multiply-accumulate
+ * kernel (Alg. 2 lines 8-14; the bounded waits have no counterpart in the
+ * paper).  From the next LT call on, that kernel's per-step waits give up
+ * after wait_limit_ns (0 = the default of about one second; at most 5 s),
+ * and its step starve_step is never issued, so that the wait on that
+ * step's barrier runs out in every CTA (0xFFFFFFFF = no step is starved).
+ * A CTA whose wait gives up stops, waits with the default limit for the
+ * copies it has in flight, and raises the context's device flag: the next
+ * ckks_device_status reports CKKS_ETIMEOUT and the results are garbage.
+ * Faults nothing.  Reset with (0, 0xFFFFFFFF).  Not for production use; it
+ * changes the context like an upload (no evaluation call may overlap it). */
+ckks_status ckks_debug_diag_mac_waits(ckks_ctx* ctx, uint64_t wait_limit_ns, uint32_t starve_step);
 
 const char* ckks_last_error(void);
 size_t ckks_device_bytes_in_use(const ckks_ctx* ctx);

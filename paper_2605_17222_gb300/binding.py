@@ -82,6 +82,7 @@ def lib():
         "ckks_decompose": [P, U32, P, I32, P, P],
         "ckks_ks_inner": [P, U32, P, I32, I32, P, I, P, P, I, P],
         "ckks_moddown": [P, U32, P, P, P],
+        "ckks_moddown_noalloc": [P, U32, P, P, P],
         "ckks_moddown_rescale": [P, U32, P, P, P],
         "ckks_rescale": [P, U32, P, P, P],
         "ckks_automorphism": [P, U32, P, I32, P, P],
@@ -92,6 +93,7 @@ def lib():
         "lt_graph_end": [P, P, PP],
         "lt_graph_destroy": [P],
         "ckks_selftest_bounded_wait": [P, U32, P],
+        "ckks_debug_diag_mac_waits": [P, ctypes.c_uint64, U32],
         "ckks_profile_enable": [ctypes.c_char_p, I],
         "ckks_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
         "ckks_profile_work": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -254,6 +256,10 @@ class Context:
 
     def selftest_bounded_wait(self, limit_ms: int = 200, stream=None) -> None:
         check(lib().ckks_selftest_bounded_wait(self.h, limit_ms, _stream(stream)))
+
+    def debug_diag_mac_waits(self, wait_limit_ns: int = 0, starve_step: int = 0xFFFFFFFF) -> None:
+        """Failure-detection test hook (ckks_debug_diag_mac_waits); (0, 0xFFFFFFFF) resets it."""
+        check(lib().ckks_debug_diag_mac_waits(self.h, int(wait_limit_ns), int(starve_step)))
 
     def bytes_in_use(self) -> int:
         return lib().ckks_device_bytes_in_use(self.h)
@@ -449,6 +455,11 @@ class Context:
         torch = _torch()
         out = out if out is not None else torch.empty((level, self.N), dtype=torch.int64, device=x.device)
         check(lib().ckks_moddown(self.h, level, _ptr(x), _ptr(out), _stream(stream)))
+        return out
+
+    def moddown_noalloc(self, x, level: int, out, stream=None):
+        """ModDown into caller-provided `out` through ckks_moddown_noalloc (no device allocation)."""
+        check(lib().ckks_moddown_noalloc(self.h, level, _ptr(x), _ptr(out), _stream(stream)))
         return out
 
     def moddown_rescale(self, x, level: int, out=None, stream=None):

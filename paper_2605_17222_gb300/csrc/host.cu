@@ -141,6 +141,9 @@ struct ckks_ctx {
     std::map<std::tuple<int, u32, u32, int32_t, int32_t>, lt_split> tuned;  // (algo, level, D, stride, offset0 mod N/2)
     mutable std::mutex mu;
     size_t bytes = 0;
+    // failure-detection test hook of the staged diagonal kernel (ckks_debug_diag_mac_waits)
+    u64 dbg_wait_ns = 0;
+    u32 dbg_starve_step = ~0u;
     // fork/join lanes of lt_eval_batch: independent groups run on the caller's
     // stream and up to FORK_LANES - 1 more, so that one group's NTT-bound
     // phases overlap another's HBM-bound diagonal multiply-accumulate
@@ -183,7 +186,11 @@ struct ckks_ctx {
     }
     u64* upload(const std::vector<u64>& v) {
         u64* p = dalloc(v.size());
-        CK(cudaMemcpy(p, v.data(), v.size() * sizeof(u64), cudaMemcpyHostToDevice));
+        const cudaError_t e = cudaMemcpy(p, v.data(), v.size() * sizeof(u64), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {  // the block is not stored anywhere yet: free and uncount it here
+            dfree(p, v.size());
+            CK(e);
+        }
         return p;
     }
 
@@ -495,6 +502,8 @@ DiagMacArgs dm_base(ckks_ctx* C, u32 level, bool with_p, const ckks_diags* f) {
     a.log_n = C->log_n;
     a.diag_level = f->level;
     a.err = (u32*)C->d_err.p;
+    a.wait_ns = C->dbg_wait_ns;
+    a.starve_step = C->dbg_starve_step;
     a.batch = 1;
     return a;
 }
@@ -997,6 +1006,15 @@ ckks_status ckks_selftest_bounded_wait(ckks_ctx* ctx, uint32_t limit_ms, void* s
         CK(cudaSetDevice(ctx->device));
         launch_wait_selftest((u32*)ctx->d_err.p, (u64)limit_ms * 1000000ull, (cudaStream_t)stream);
         CK(cudaGetLastError());
+    });
+}
+
+ckks_status ckks_debug_diag_mac_waits(ckks_ctx* ctx, uint64_t wait_limit_ns, uint32_t starve_step) {
+    return guarded([&] {
+        if (!ctx) fail(CKKS_EINVAL, "null argument");
+        if (wait_limit_ns > 5000000000ull) fail(CKKS_EINVAL, "wait limit above 5 s");
+        ctx->dbg_wait_ns = wait_limit_ns;
+        ctx->dbg_starve_step = starve_step;
     });
 }
 
@@ -1849,9 +1867,10 @@ ckks_status ckks_moddown(ckks_ctx* ctx, uint32_t level, const uint64_t* x, uint6
 }  // extern "C"
 
 // ------------------------------------------------------------------ ModDown without allocation
-// For callers that must not allocate device memory while they run: code
-// recorded into a CUDA graph, code running under an external memory budget
-// or allocator, or code on a path that may not call cudaMalloc at all.
+// For host programs that cannot let the library allocate device memory while
+// it runs: an application that manages all GPU memory through its own
+// allocator or budget, or a latency-bound path where a cudaMalloc (and the
+// device synchronisation it may imply) is not acceptable.
 // ModDown's only scratch (the inverse-transformed special-prime limbs) lives
 // in this fixed file-scope array instead of the stream-ordered pool: at most
 // NOALLOC_SCRATCH_WORDS words (8 limbs of N = 2^16, 4 MiB), held by every

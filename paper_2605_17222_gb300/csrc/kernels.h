@@ -143,6 +143,12 @@ struct DiagMacArgs {
     u32 level, ext, L, k_p, beta, log_n;
     u32 n1, n2, n3, lift0, diag_level;
     u32* err;                        // set to nonzero when a bounded device wait gives up
+    // Failure-detection test hook of the staged kernel: the step loop's
+    // waits give up after wait_ns (0: the default of one second), and step
+    // starve_step (~0u: none) is never issued, so that its wait runs out.
+    // The drain of copies in flight always keeps the default limit.
+    u64 wait_ns;
+    u32 starve_step;
     // Batch of ciphertexts sharing the diagonals and keys: ciphertext b uses
     // c0[b], c1[b] as its lifted inputs and A[i] + b*bs_ab, B[i] + b*bs_ab,
     // Dg[i] + b*bs_dg, U0/U1[k] + b*bs_u for the rest.  CTAs of the same

@@ -291,11 +291,11 @@ __device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(u64* bar, u32 parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(u64* bar, u32 parity, u64 limit_ns = DM_WAIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const u64 t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > DM_WAIT_NS) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, u32 bytes, u64* bar) {
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
     for (u32 jj = l; jj < n2; jj += RUN) srun_of[jj] = jj ? auto_src(run * RUN, a.gal_mid[jj], a.log_n) / RUN : run;
 
     auto issue = [&](u32 it) {
-        if (it >= n1n2) return;
+        if (it >= n1n2 || it == a.starve_step) return;
         const u32 j = n1 == 1 ? it : it / n1, i = n1 == 1 ? 0u : it % n1;
         u64* st = smem + (size_t)(it % NS) * stage_runs * RUN;
         u64* bar = &full_bar[it % NS];
@@ -400,7 +400,8 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
     for (int kk = 0; kk < K3; kk++) acc0[kk] = acc1[kk] = U128{0, 0};
     u32 terms = 0;
     u32 issued = NS - 1;  // steps the producer has issued (meaningful in thread 0)
-    bool failed = false;
+    u32 failed_at = n1n2;  // the step whose wait gave up (n1n2: none)
+    const u64 wait_ns = a.wait_ns ? a.wait_ns : DM_WAIT_NS;
     u64 k0[KB], k1[KB];  // switching-key words of the current giant index at this thread's position
     u32 pm = 0;          // in-run source position of the middle-layer gather of the current j
 
@@ -418,10 +419,10 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
             }
             pm = auto_src(s, a.gal_mid[j], a.log_n) % RUN;
         }
-        const bool ok = mbar_wait_bounded(&full_bar[it % NS], (it / NS) & 1);
+        const bool ok = mbar_wait_bounded(&full_bar[it % NS], (it / NS) & 1, wait_ns);
         // everyone has finished step it-1 (its buffer is free) and agrees on success
         if (__syncthreads_or(!ok)) {
-            failed = true;
+            failed_at = it;
             break;
         }
         if (l == 0) {
@@ -485,11 +486,15 @@ __global__ void __launch_bounds__(RUN, 1) k_diag_mac_staged(const __grid_constan
             }
         }
     }
-    if (failed) {
-        // drain: the producer waits (bounded) for every step it issued that was not consumed
+    if (failed_at < n1n2) {
+        // drain: the producer waits (bounded, default limit) for the steps it
+        // issued that were not consumed, failed_at .. issued - 1.  Every step
+        // before failed_at completed and was consumed; their stages have been
+        // reused or never will be, so waiting on them would only run out.
+        // A starved step has no copies in flight.
         if (l == 0) {
-            for (u32 it = 0; it < min(issued, n1n2); it++)
-                mbar_wait_bounded(&full_bar[it % NS], (it / NS) & 1);
+            for (u32 it = failed_at; it < min(issued, n1n2); it++)
+                if (it != a.starve_step) mbar_wait_bounded(&full_bar[it % NS], (it / NS) & 1);
             atomicExch(a.err, 1u);
         }
         return;

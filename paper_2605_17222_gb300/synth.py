@@ -127,6 +127,8 @@ def param_set(name: str) -> ParamSet:
     n14  : N=2^14, Q = 50b + 7x40b (8 limbs), P = 2x60b, dnum 4 (alpha 2)
     setA : the paper's Set-A shape, N=2^13, L+1=5, alpha=5, beta=1, 54-bit words
     setB : the paper's Set-B shape, N=2^15, L+1=16, alpha=8, beta=2, 54-bit words
+    n16d8, n14d8, n15d16 : n16 / n14 / n15 with more digits (dnum 8, 8, 16: beta 8, 8, 16),
+           the shapes where the staged diagonal kernel's 6-digit key registers do not suffice
     """
     if name in _CACHE:
         return _CACHE[name]
@@ -143,6 +145,12 @@ def param_set(name: str) -> ParamSet:
         ps = make_params("setA", 13, [54] * 5, [54] * 5, 1)
     elif name == "setB":
         ps = make_params("setB", 15, [54] * 16, [54] * 8, 2)
+    elif name == "n16d8":
+        ps = make_params("n16d8", 16, [55] + [40] * 23, [60] * 4, 8)
+    elif name == "n14d8":
+        ps = make_params("n14d8", 14, [50] + [40] * 7, [60] * 2, 8)
+    elif name == "n15d16":
+        ps = make_params("n15d16", 15, [50] + [40] * 15, [60] * 3, 16)
     elif name == "tiny":  # unit-test size
         ps = make_params("tiny", 5, [50, 40, 40, 40], [60, 60], 2)
     else:

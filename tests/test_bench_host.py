@@ -44,12 +44,19 @@ def test_alu_fraction_adds_the_two_kinds_of_work():
 
 
 def test_diag_mac_bytes_at_the_headline_split():
-    """(1,64,4), level 24, k 4, beta 6, 256 diagonals: 256 x 28 diagonal limbs,
-    63 giant indices x 2 x 6 x 28 key limbs, one baby index's 6 x 28 digit
-    limbs, the 2 x 24 input limbs and 4 x 2 x 28 output limbs."""
-    want = (256 * 28 + 63 * 336 + 168 + 48 + 224) * LIMB
-    assert want == 15_086_911_488
+    """(1,64,4), level 24, k 4, beta 6, 256 diagonals: the compulsory words K6
+    streams -- 256 x 28 diagonal limbs and 63 middle-layer keys of 2 x 6 x 28
+    limbs -- 14.86 GB; digits, inputs and partial sums are intermediates."""
+    want = (256 * 28 + 63 * 336) * LIMB
+    assert round(want / 1e9, 2) == 14.86
     assert bench.algorithmic_bytes("diag_mac", (1, 64, 4), 24, 4, 6, 256, 2 ** 16) == (want, 1)
+    # no middle layer (DH as TH(n1, 1, n3)): diagonals only
+    assert bench.algorithmic_bytes("diag_mac", (16, 1, 16), 24, 4, 6, 256, 2 ** 16) == (256 * 28 * LIMB, 1)
+
+
+def test_ks_inner_bytes_are_the_inner_and_outer_keys():
+    """(4,8,8): 3 inner-layer and 7 outer-layer keys of 2 x 6 x 28 limbs, over 10 products."""
+    assert bench.algorithmic_bytes("ks_inner", (4, 8, 8), 24, 4, 6, 256, 2 ** 16) == (10 * 336 * LIMB, 10)
 
 
 def test_lt_compulsory_bytes():

@@ -28,3 +28,41 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     g.ntt(t, ps.L, ext=True, inverse=True)
     torch.cuda.synchronize()
     assert np.array_equal(binding.to_host(t), a)
+
+
+def test_diag_mac_waits_run_out_in_the_production_kernel():
+    """The staged diagonal kernel itself: with its test hook, step 1 is never
+    issued and the step loop's waits give up after 20 us.  Every CTA stops,
+    drains its copies in flight, the host reads CKKS_ETIMEOUT, the call comes
+    back within milliseconds, and with the hook reset the same context
+    computes the LT bit-exactly."""
+    import time
+
+    import torch
+
+    from oracle.workload import make_problem
+
+    from gpu_common import assert_same, ensure_keys, gpu_context, oracle_lt, upload_problem
+
+    pb = make_problem("toy", 0, 64)
+    split = (4, 4, 4)
+    ensure_keys(pb, "th", split)
+    g = gpu_context("toy")
+    f = upload_problem(g, pb)
+    ct = g.ct_from_host(np.stack(pb.ct))
+    g.lt_eval(ct, f, "th", split)  # warm: per-level tables, kernel attributes
+    g.device_status()
+    g.debug_diag_mac_waits(20_000, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.lt_eval(ct, f, "th", split)
+    with pytest.raises(binding.CkksError) as e:
+        g.device_status()
+    elapsed = time.perf_counter() - t0
+    assert e.value.status == CKKS_ETIMEOUT
+    assert elapsed < 0.25, f"the failing LT took {elapsed:.3f} s (a wait or the drain used the 1 s default)"
+    g.debug_diag_mac_waits(0, 0xFFFFFFFF)
+    g.device_status()  # the flag was cleared
+    out, _ = g.lt_eval(ct, f, "th", split)
+    assert_same(out.numpy(), oracle_lt(pb, "th", split), "after the timeout")
+    g.device_status()

@@ -1,0 +1,85 @@
+"""Parity of the benchmarked configuration and of the diagonal kernels' fallbacks.
+
+* The headline split: TH-BSGS (1, 64, 4) at full size (N = 2^16, 24 Q limbs,
+  4 special primes, dnum 6, 256 consecutive diagonals, seed 1), the split the
+  measuring autotuner picks for the benchmark, bit for bit with the oracle and
+  within 1e-4 of the FP64 product (Algorithm 2).
+* The hoisted diagonal method at full size, TH(1, 64, 1) and lt_eval's own
+  LT_DIAG, on the first 64 diagonals of the same matrix (the keys 1..63 the
+  headline split already needs; all 256 would need 255 keys, 45 GB of oracle
+  memory): bit for bit, and TH(1, D, 1) identical to the diagonal method.
+* Contexts with more than six digits (beta = 8 at N = 2^14 and N = 2^16, and
+  beta = 16 at N = 2^15): the staged diagonal kernel keeps six digits of key
+  words in registers, so these shapes take the plain kernel -- the unrolled
+  digit loop for beta <= 8 and the rolled one beyond -- bit for bit with the
+  oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import lt as olt
+from oracle.workload import add_keys, make_problem
+
+from gpu_common import assert_same, ensure_keys, gpu_context, oracle_lt, upload_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def max_err(pb, ct, fvals=None):
+    y = pb.decrypt((ct[0], ct[1]))
+    want = pb.expected() if fvals is None else olt.fp64_reference(pb.z, fvals, pb.stride, pb.offset0)
+    e = y - want
+    return float(np.max(np.maximum(np.abs(e.real), np.abs(e.imag))))
+
+
+@pytest.fixture(scope="module")
+def headline():
+    pb = make_problem("n16", 1, 256)
+    ensure_keys(pb, "th", (1, 64, 4))
+    g = gpu_context("n16")
+    f = upload_problem(g, pb)
+    yield pb, g, f
+    g.close()
+
+
+def test_headline_split_bit_exact(headline):
+    pb, g, f = headline
+    out, chosen = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, "th", (1, 64, 4))
+    assert chosen == (1, 64, 4)
+    got = out.numpy()
+    assert_same(got, oracle_lt(pb, "th", (1, 64, 4)), "full TH (1,64,4)")
+    assert max_err(pb, got) <= 1e-4
+
+
+def test_diagonal_method_full_size(headline):
+    pb, g, _ = headline
+    D = 64
+    f64 = g.upload_diagonals(pb.diags[:D], stride=1, level=pb.ctx.L)
+    ct = g.ct_from_host(np.stack(pb.ct))
+    a, _ = g.lt_eval(ct, f64, "diag")
+    b, _ = g.lt_eval(ct, f64, "th", (1, D, 1))
+    want, _ = olt.run(pb.ctx, "diag", pb.ct, pb.diags[:D], pb.keys)
+    got = a.numpy()
+    assert_same(got, np.stack(want), "full diagonal method, 64 diagonals")
+    assert_same(b.numpy(), got, "TH(1,64,1) vs diagonal method")
+    assert max_err(pb, got, pb.fvals[:D]) <= 1e-5
+    f64.free()
+
+
+@pytest.mark.parametrize("name,D,algo,split", [
+    ("n14d8", 16, "th", (2, 4, 2)),
+    ("n14d8", 16, "dh", (4, 4)),
+    ("n15d16", 16, "th", (2, 4, 2)),
+    ("n16d8", 32, "th", (2, 4, 4)),
+])
+def test_more_digits_than_the_staged_kernel_holds(name, D, algo, split):
+    pb = make_problem(name, 5, D)
+    assert pb.ctx.beta(pb.level) > 6
+    ensure_keys(pb, algo, split)
+    g = gpu_context(name)
+    f = upload_problem(g, pb)
+    out, _ = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, algo, split)
+    got = out.numpy()
+    assert_same(got, oracle_lt(pb, algo, split), f"{name} {algo} {split}")
+    assert max_err(pb, got) <= 1e-5
+    g.close()
