@@ -580,6 +580,11 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
     a.B[0] = io.c1;
     a.c0[0] = io.c0;
     a.c1[0] = io.c1;
+    {  // P c0 once (line 2), read by every middle-layer step of the first baby index
+        u64* c0l = ar.limbs(level);
+        launch_lift((const ModC*)C->d_mods.p, C->d_lift.p, C->d_lift_sh.p, &io.c0, &c0l, 1, level, C->log_n, st);
+        a.c0l[0] = c0l;
+    }
     for (u32 i = 1; i < n1; i++) a.A[i] = A[i], a.B[i] = B[i];
     for (u32 i = 0; i < n1; i++) a.Dg[i] = Dg[i];
     for (u32 j = 1; j < n2; j++) {
@@ -713,6 +718,18 @@ void sched_th_batch(ckks_ctx* C, u32 level, const std::vector<LtIO>& ios, const 
     a.lift0 = 1;
     a.batch = nbat;
     for (u32 b = 0; b < nbat; b++) a.c0[b] = ios[b].c0, a.c1[b] = ios[b].c1;
+    {  // P c0 once per ciphertext (line 2)
+        std::vector<const u64*> cin;
+        std::vector<u64*> cout;
+        u64* c0l = ar.limbs((size_t)nbat * level);
+        for (u32 b = 0; b < nbat; b++) {
+            cin.push_back(ios[b].c0);
+            cout.push_back(c0l + (size_t)b * level * N);
+            a.c0l[b] = cout.back();
+        }
+        launch_lift((const ModC*)C->d_mods.p, C->d_lift.p, C->d_lift_sh.p, cin.data(), cout.data(), nbat, level,
+                    C->log_n, st);
+    }
     for (u32 i = 0; i < n1; i++) a.A[i] = Ap(0, i), a.B[i] = Bp(0, i), a.Dg[i] = Dp(0, i);
     a.bs_ab = (u64)n1 * ext * N;
     a.bs_dg = (u64)n1 * dig * N;

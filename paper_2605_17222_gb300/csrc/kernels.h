@@ -158,8 +158,15 @@ struct DiagMacArgs {
     u64 bs_ab, bs_dg, bs_u;
     const u64* c0[DM_MAX_B];
     const u64* c1[DM_MAX_B];
+    // P c0 per ciphertext (Q limbs [level][N], from launch_lift), or null:
+    // the lifted input of Alg. 2 line 2 computed once instead of at every step
+    const u64* c0l[DM_MAX_B];
 };
 void launch_diag_mac(const DiagMacArgs& a, cudaStream_t st);
+// out_i[t][s] = in_i[t][s] * [P]_{q_t} mod q_t for t < level (Alg. 2 line 2,
+// the Q limbs of P c0; the P limbs are zero and not stored), i < count.
+void launch_lift(const ModC* mods, const u64* lift_c, const u64* lift_sh, const u64* const* in, u64* const* out,
+                 u32 count, u32 level, u32 log_n, cudaStream_t st);
 void launch_wait_selftest(u32* err, u64 limit_ns, cudaStream_t st);
 
 uint64_t launches();

@@ -15,7 +15,9 @@
 // reduced once (PE modes CWPM-ACC / CM-ACC of Sec. V, done lazily).
 #include "kernels.h"
 
+#include <algorithm>
 #include <atomic>
+#include <cstdlib>
 
 namespace ckks {
 namespace {
@@ -523,6 +525,285 @@ __global__ void k_wait_selftest(u32* err, u64 limit_ns) {
     if (!ok) atomicExch(err, 1u);
 }
 
+// ------------------------------------------------------------------ K6, warp-specialised
+// The same computation again, with the copies issued by a warp of their own.
+// A CTA has RUN compute threads (one position each) and one producer warp.
+// Every operand of a step, the middle layer's switching-key runs included,
+// arrives in a shared-memory stage by bulk copies; the ring has NS stages,
+// ordered by two mbarriers per stage and no CTA-wide barrier in the loop:
+//   full[s]  : the producer's expect_tx; the stage's copies complete it.
+//   empty[s] : one arrival per compute warp once the warp has read the stage;
+//              the producer waits on it before it refills the stage.
+// A compute warp therefore never waits for another compute warp, and the
+// producer never waits inside a compute warp's step.
+//
+// Every wait is bounded (compute: wait_ns, default 1 s; producer: 1 s) and
+// also gives up as soon as the CTA's abort flag is raised.  A warp whose wait
+// gives up raises the flag and leaves its loop (all its lanes together); the
+// producer stops issuing.  Each thread then reaches one final named barrier
+// exactly once; after it, if the flag is up, the producer waits (1 s limit)
+// for the last copies it issued into each stage -- a stage is only refilled
+// after every warp consumed it, so at most one phase of each full barrier is
+// pending -- sets *err, and the CTA writes no output.
+__device__ __forceinline__ void nbar_sync(u32 id, u32 count) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(u64* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_abortable(u64* bar, u32 parity, u64 limit_ns, const volatile u32* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const u64 t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (*abort || global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+template <int K3, int RUN, int NS, int BETA>
+struct WsLayout {
+    // one stage, in words: K3 diagonal runs | BETA digit runs | A run | B run | BETA key runs (word pairs)
+    static constexpr u32 OFF_DIG = K3 * RUN;
+    static constexpr u32 OFF_A = (K3 + BETA) * RUN;
+    static constexpr u32 OFF_B = OFF_A + RUN;
+    static constexpr u32 OFF_KEY = OFF_B + RUN;
+    static constexpr u32 STAGE = OFF_KEY + 2 * BETA * RUN;
+    static constexpr size_t bytes(u32 n2) { return 8ull * STAGE * NS + ((4ull * n2 + 15) & ~15ull); }
+};
+
+template <int K3, int RUN, int NS, int BETA>
+__global__ void __launch_bounds__(RUN + 32, 1) k_diag_mac_ws(const __grid_constant__ DiagMacArgs a) {
+    using LY = WsLayout<K3, RUN, NS, BETA>;
+    constexpr u32 NT = RUN + 32;  // threads of the CTA
+    constexpr u32 RB = RUN * 8;   // bytes per run
+    constexpr u32 FULL = 0xffffffffu;
+    extern __shared__ __align__(128) u64 smem[];
+    __shared__ __align__(8) u64 full_bar[NS];
+    __shared__ __align__(8) u64 empty_bar[NS];
+    __shared__ u32 abort_flag;
+    const u32 N = 1u << a.log_n;
+    const u32 l = threadIdx.x;
+    const u32 bidx = blockIdx.x % a.batch;
+    const u32 run = blockIdx.x / a.batch;
+    const size_t oab = bidx * a.bs_ab, odg = bidx * a.bs_dg, ou = bidx * a.bs_u;
+    const u32 t = blockIdx.y;
+    const u32 k_first = blockIdx.z * K3;
+    const u32 k_count = min((u32)K3, a.n3 - k_first);
+    const u32 gmod = t < a.level ? t : a.L + (t - a.level);
+    const u32 drow = t < a.level ? t : a.diag_level + (t - a.level);
+    const ModC m = a.mods[gmod];
+    const size_t dstride = (size_t)(a.diag_level + a.k_p) * N;
+    const size_t plane = (size_t)(a.L + a.k_p) * N;  // key pairs per digit
+    const size_t dig_b = (size_t)a.ext * N;
+    const size_t tN = (size_t)t * N;
+    const u32 n1 = a.n1, n2 = a.n2, n1n2 = n1 * n2;
+    const u32 beta = n2 > 1 ? a.beta : 0;  // <= BETA (host checks)
+    const bool lift_limb = a.lift0 && t < a.level;
+    const u64* c0l = a.c0l[bidx];
+    u32* srun_of = (u32*)(smem + (size_t)NS * LY::STAGE);
+    for (u32 jj = l; jj < n2; jj += NT) srun_of[jj] = jj ? auto_src(run * RUN, a.gal_mid[jj], a.log_n) / RUN : run;
+    if (l == 0) {
+#pragma unroll
+        for (int b = 0; b < NS; b++) {
+            mbar_init(&full_bar[b], 1);
+            mbar_init(&empty_bar[b], RUN / 32);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    volatile u32* abort = &abort_flag;
+
+    if (l >= RUN) {
+        // ------------------------------------------------------------ producer warp
+        const u32 ln = l - RUN;
+        const u64* A0 = a.lift0 ? (c0l ? c0l : a.c0[bidx]) : a.A[0];
+        const u64* B0 = a.lift0 ? a.c1[bidx] : a.B[0];
+        // lane c < K3 keeps the source run of diagonal c's gather
+        u32 hrun = 0;
+        if (ln < (u32)K3) {
+            const u32 kc = k_first + min(ln, k_count - 1);
+            const u32 g = a.gal_diag[kc];
+            hrun = (g ? auto_src(run * RUN, g, a.log_n) : run * RUN) / RUN;
+        }
+        u32 last[NS];  // the last step issued into each stage (lane 0)
+#pragma unroll
+        for (int b = 0; b < NS; b++) last[b] = ~0u;
+        for (u32 it = 0; it < n1n2; it++) {
+            const u32 sidx = it % NS;
+            bool go = true;
+            if (ln == 0) {
+                if (it >= NS && !mbar_wait_abortable(&empty_bar[sidx], ((it - NS) / NS) & 1, DM_WAIT_NS, abort))
+                    *abort = 1u;  // every compute warp has read step it - NS, or giving up
+                go = !*abort;
+            }
+            if (!__shfl_sync(FULL, go, 0)) break;
+            if (it == a.starve_step) continue;  // test hook: this step is never issued
+            const u32 j = n1 == 1 ? it : it / n1, i = n1 == 1 ? 0u : it % n1;
+            const bool lifted = (i == 0) && a.lift0;
+            const bool copy_a = !lifted || lift_limb;
+            const u32 n_ab = j == 0 ? (copy_a ? 2u : 0u) : (copy_a ? 1u : 0u);
+            const u32 n_dig = j == 0 ? 0u : beta;
+            u64* st = smem + (size_t)sidx * LY::STAGE;
+            u64* bar = &full_bar[sidx];
+            if (ln == 0) {
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_expect_tx(bar, (k_count + 3 * n_dig + n_ab) * RB);
+                last[sidx] = it;
+            }
+            __syncwarp();
+            // one copy per lane: diagonals, digits, A (and B), keys
+            const u32 srun = srun_of[j];
+            const u32 c = ln;
+            if (c < k_count) {
+                const size_t didx = (size_t)(n1 * j + i) * dstride + (size_t)drow * N;
+                tma_load_1d(st + (size_t)c * RUN,
+                            a.diags + (size_t)(n1n2 * (k_first + c)) * dstride + didx + (size_t)hrun * RUN, RB, bar);
+            } else if (c >= (u32)K3 && c < (u32)K3 + n_dig) {
+                const u32 b = c - K3;
+                tma_load_1d(st + LY::OFF_DIG + (size_t)b * RUN, a.Dg[i] + odg + b * dig_b + tN + (size_t)srun * RUN,
+                            RB, bar);
+            } else if (c == (u32)(K3 + BETA) && n_ab >= 1) {
+                const u64* Ai = i ? a.A[i] + oab : A0;
+                tma_load_1d(st + LY::OFF_A, Ai + tN + (size_t)srun * RUN, RB, bar);
+            } else if (c == (u32)(K3 + BETA + 1) && n_ab == 2) {
+                const u64* Bi = i ? a.B[i] + oab : B0;
+                tma_load_1d(st + LY::OFF_B, Bi + tN + (size_t)srun * RUN, RB, bar);
+            } else if (c >= (u32)(K3 + BETA + 2) && c < (u32)(K3 + BETA + 2) + n_dig) {
+                const u32 b = c - (K3 + BETA + 2);
+                tma_load_1d(st + LY::OFF_KEY + (size_t)b * 2 * RUN,
+                            a.keys[j] + 2 * ((size_t)b * plane + (size_t)gmod * N + (size_t)run * RUN), 2 * RB, bar);
+            }
+        }
+        nbar_sync(1, NT);  // every thread of the CTA reaches this once
+        if (*abort && ln == 0) {
+            // drain: the last phase issued into each stage (the earlier ones completed and were consumed)
+#pragma unroll
+            for (int b = 0; b < NS; b++)
+                if (last[b] != ~0u) mbar_wait_bounded(&full_bar[b], (last[b] / NS) & 1);
+            atomicExch(a.err, 1u);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- compute threads
+    const u32 s = run * RUN + l;
+    const u64 wait_ns = a.wait_ns ? a.wait_ns : DM_WAIT_NS;
+    const u64 lc = lift_limb ? a.lift_c[gmod] : 0, lsh = lift_limb ? a.lift_sh[gmod] : 0;
+    const bool fold = m.q < (1ull << 41) && beta <= 8;
+    const u64 c63 = fold ? (1ull << 63) % m.q : 0, c64 = fold ? (0 - m.q) % m.q : 0;  // 2^63, 2^64 mod q
+    u32 pd[K3];
+#pragma unroll
+    for (int kk = 0; kk < K3; kk++) {
+        const u32 kc = k_first + min((u32)kk, k_count - 1);
+        const u32 g = a.gal_diag[kc];
+        const u32 hr = (g ? auto_src(run * RUN, g, a.log_n) : run * RUN) / RUN;
+        pd[kk] = (g ? auto_src(s, g, a.log_n) : s) - hr * RUN;
+    }
+    U128 acc0[K3], acc1[K3];
+#pragma unroll
+    for (int kk = 0; kk < K3; kk++) acc0[kk] = acc1[kk] = U128{0, 0};
+    u32 terms = 0;
+    for (u32 it = 0; it < n1n2; it++) {
+        const u32 sidx = it % NS;
+        // the warp decides together, so that its lanes stay converged
+        if (!__all_sync(FULL, mbar_wait_abortable(&full_bar[sidx], (it / NS) & 1, wait_ns, abort))) {
+            *abort = 1u;
+            break;
+        }
+        const u32 j = n1 == 1 ? it : it / n1, i = n1 == 1 ? 0u : it % n1;
+        const bool lifted = (i == 0) && a.lift0;
+        const u64* st = smem + (size_t)sidx * LY::STAGE;
+        u64 av, bv;
+        if (j == 0) {
+            if (lifted) {
+                if (lift_limb) {
+                    const u64 x = st[LY::OFF_A + l];
+                    av = c0l ? x : mul_shoup(x, lc, lsh, m.q);
+                    bv = mul_shoup(st[LY::OFF_B + l], lc, lsh, m.q);
+                } else {
+                    av = bv = 0;
+                }
+            } else {
+                av = st[LY::OFF_A + l];
+                bv = st[LY::OFF_B + l];
+            }
+        } else {
+            const u32 pm = auto_src(s, a.gal_mid[j], a.log_n) % RUN;
+            U128 x0{0, 0}, x1{0, 0};
+            const ulonglong2* kp = (const ulonglong2*)(st + LY::OFF_KEY) + l;
+#pragma unroll
+            for (int b = 0; b < BETA; b++) {
+                if (b < (int)beta) {
+                    const u64 d = st[LY::OFF_DIG + b * RUN + pm];
+                    const ulonglong2 kv = kp[b * RUN];
+                    mac128(x0, d, kv.x);
+                    mac128(x1, d, kv.y);
+                }
+            }
+            if (lifted) {
+                if (lift_limb) {
+                    const u64 x = st[LY::OFF_A + pm];
+                    add128(x0, c0l ? x : mul_shoup(x, lc, lsh, m.q));
+                }
+            } else {
+                add128(x0, st[LY::OFF_A + pm]);
+            }
+            // partial reductions feed the products (see k_diag_mac_staged)
+            if (fold) {
+                av = (x0.lo & ~(1ull << 63)) + ((x0.lo >> 63) ? c63 : 0) + x0.hi * c64;
+                bv = (x1.lo & ~(1ull << 63)) + ((x1.lo >> 63) ? c63 : 0) + x1.hi * c64;
+            } else {
+                av = reduce128_lazy(x0, m);
+                bv = reduce128_lazy(x1, m);
+            }
+        }
+        u64 f[K3];
+#pragma unroll
+        for (int kk = 0; kk < K3; kk++) f[kk] = kk < (int)k_count ? st[kk * RUN + pd[kk]] : 0;
+        __syncwarp();
+        if ((l & 31) == 0) mbar_arrive(&empty_bar[sidx]);  // the warp has read stage sidx
+#pragma unroll
+        for (int kk = 0; kk < K3; kk++) {
+            if (kk < (int)k_count) {
+                mac128(acc0[kk], av, f[kk]);
+                mac128(acc1[kk], bv, f[kk]);
+            }
+        }
+        if (++terms == 64) {  // 64 products below 2^122 each fit the accumulators
+            terms = 0;
+#pragma unroll
+            for (int kk = 0; kk < K3; kk++) {
+                acc0[kk] = U128{reduce128(acc0[kk], m), 0};
+                acc1[kk] = U128{reduce128(acc1[kk], m), 0};
+            }
+        }
+    }
+    nbar_sync(1, NT);  // every thread of the CTA reaches this once; then one decision for all
+    if (*abort) return;
+#pragma unroll
+    for (int kk = 0; kk < K3; kk++) {
+        if (kk < (int)k_count) {
+            a.U0[k_first + kk][ou + tN + s] = reduce128(acc0[kk], m);
+            a.U1[k_first + kk][ou + tN + s] = reduce128(acc1[kk], m);
+        }
+    }
+}
+
+// P x on the Q limbs (Alg. 2 line 2), for every polynomial of a batch.
+struct LiftArgs {
+    const u64* in[DM_MAX_B];
+    u64* out[DM_MAX_B];
+};
+__global__ void k_lift(const ModC* __restrict__ mods, const u64* __restrict__ lift_c, const u64* __restrict__ lift_sh,
+                       const __grid_constant__ LiftArgs p, u32 log_n) {
+    const u32 N = 1u << log_n;
+    const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+    const u32 t = blockIdx.y, i = blockIdx.z;
+    if (s >= N) return;
+    const size_t o = (size_t)t * N + s;
+    p.out[i][o] = mul_shoup(p.in[i][o], lift_c[t], lift_sh[t], mods[t].q);
+}
+
 constexpr size_t DM_SMEM_MAX = 226 * 1024;  // dynamic part; the mbarriers take a few static bytes
 
 template <int K3, int RUN, int NS, int KB>
@@ -557,8 +838,52 @@ bool try_staged(const DiagMacArgs& a, cudaStream_t st) {
     return true;
 }
 
+template <int K3, int RUN, int NS, int BETA>
+bool try_ws(const DiagMacArgs& a, cudaStream_t st) {
+    using LY = WsLayout<K3, RUN, NS, BETA>;
+    const u32 beta = a.n2 > 1 ? a.beta : 0;
+    const size_t sm = LY::bytes(a.n2);
+    const u32 N = 1u << a.log_n;
+    if (sm > DM_SMEM_MAX || N % RUN || beta > (u32)BETA) return false;
+    static std::atomic<uint64_t> attr_set{0}, attr_bad{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return false;
+    }
+    const uint64_t bit = 1ull << dev;
+    if (attr_bad.load(std::memory_order_relaxed) & bit) return false;
+    if (!(attr_set.load(std::memory_order_acquire) & bit)) {
+        if (cudaFuncSetAttribute(k_diag_mac_ws<K3, RUN, NS, BETA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)DM_SMEM_MAX) != cudaSuccess) {
+            cudaGetLastError();
+            attr_bad.fetch_or(bit, std::memory_order_relaxed);
+            return false;
+        }
+        attr_set.fetch_or(bit, std::memory_order_release);
+    }
+    const dim3 grid((N / RUN) * a.batch, a.ext, (a.n3 + K3 - 1) / K3);
+    k_diag_mac_ws<K3, RUN, NS, BETA><<<grid, RUN + 32, sm, st>>>(a);
+    return true;
+}
+
+// Which K6 form runs: the warp-specialised one when it fits (0), else the
+// CTA-barrier staged one; CKKS_K6_FORM=1 forces the latter (comparisons).
+static int k6_form() {
+    static const int f = [] {
+        const char* e = getenv("CKKS_K6_FORM");
+        return e ? atoi(e) : 0;
+    }();
+    return f;
+}
+
 template <int K3>
 bool launch_staged(const DiagMacArgs& a, cudaStream_t st) {
+    if (k6_form() == 0) {
+        // 512 positions per CTA; 256 with eight outer accumulators per thread (register budget)
+        constexpr int RUN = K3 >= 8 ? 256 : 512;
+        if (a.n2 > 1 ? try_ws<K3, RUN, 2, 6>(a, st) : try_ws<K3, RUN, 4, 0>(a, st)) return true;
+    }
     return try_staged<K3, 512, 4, 6>(a, st) || try_staged<K3, 512, 3, 6>(a, st) || try_staged<K3, 256, 4, 6>(a, st);
 }
 
@@ -578,6 +903,18 @@ void launch_interleave_key(const u64* in, u64* out, size_t plane, u32 beta_max, 
     const size_t total = plane * beta_max;
     k_interleave_key<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(in, (ulonglong2*)out, plane, total);
     count_launch();
+}
+
+void launch_lift(const ModC* mods, const u64* lift_c, const u64* lift_sh, const u64* const* in, u64* const* out,
+                 u32 count, u32 level, u32 log_n, cudaStream_t st) {
+    const u32 N = 1u << log_n;
+    for (u32 c0 = 0; c0 < count; c0 += DM_MAX_B) {
+        LiftArgs p{};
+        const u32 n = std::min<u32>(DM_MAX_B, count - c0);
+        for (u32 i = 0; i < n; i++) p.in[i] = in[c0 + i], p.out[i] = out[c0 + i];
+        k_lift<<<dim3((N + 255) / 256, level, n), 256, 0, st>>>(mods, lift_c, lift_sh, p, log_n);
+        count_launch();
+    }
 }
 
 void launch_wait_selftest(u32* err, u64 limit_ns, cudaStream_t st) {
