@@ -193,12 +193,15 @@ def algorithmic_bytes(cls: str, split, level: int, k: int, beta: int, n_diag: in
     return None, None
 
 
-def algorithmic_bytes_for(algo: str, cls: str, split, level: int, k: int, beta: int, n_diag: int, N: int) -> tuple:
-    """algorithmic_bytes for any algorithm: DH(n1, n2) runs as TH(n1, 1, n2) and
-    the diagonal method as TH(1, D, 1); BSGS multiplies over Q only (K6 without
-    the P limbs or a middle layer) and switches keys once per rotation."""
+def algorithmic_bytes_for(algo: str, cls: str, split, level: int, k: int, beta: int, n_diag: int, N: int,
+                          dh_fused: bool = False) -> tuple:
+    """algorithmic_bytes for any algorithm: DH(n1, n2) runs as TH(n1, 1, n2), or
+    as TH(1, n1, n2) with its baby steps fused into K6 (dh_fused), and the
+    diagonal method as TH(1, D, 1); BSGS multiplies over Q only (K6 without the
+    P limbs or a middle layer) and switches keys once per rotation."""
     if algo == "dh":
-        return algorithmic_bytes(cls, (split[0], 1, split[1]), level, k, beta, n_diag, N)
+        th = (1, split[0], split[1]) if dh_fused else (split[0], 1, split[1])
+        return algorithmic_bytes(cls, th, level, k, beta, n_diag, N)
     if algo == "diag":
         return algorithmic_bytes(cls, (1, n_diag, 1), level, k, beta, n_diag, N)
     if algo == "bsgs":
@@ -506,7 +509,8 @@ def run_ours(args, dist: Dist):
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
-    b_lt, n_lt = algorithmic_bytes_for(algo, dominant, split3, LEVEL, ps.k, beta, D, ps.n)
+    dh_sched = g.dh_schedule(f, LEVEL, split3) if algo == "dh" else None
+    b_lt, n_lt = algorithmic_bytes_for(algo, dominant, split3, LEVEL, ps.k, beta, D, ps.n, dh_sched == "fused")
     roof = None
     if b_lt and dom_n:
         per_launch = b_lt / n_lt
@@ -526,6 +530,7 @@ def run_ours(args, dist: Dist):
         "config": {"workload": f"single LT: N=2^16, level {LEVEL} (Q = 55b + 23x40b), 4x60b special primes, "
                                f"dnum 6, {D} consecutive diagonals, one ciphertext at the top level",
                    "algo": algo, "split": list(split3), "parallelism": f"replicas x{dist.world}",
+                   **({"dh_schedule": dh_sched} if dh_sched else {}),
                    "split_choice": ("given" if args.split else "the diagonal method has one split" if tuned_ms is None
                                     else f"autotuned over the cost model's best candidates ({tuned_ms:.3f} ms "
                                          f"when measured)"),
@@ -1161,6 +1166,16 @@ def run_serving(args, dist: Dist):
     lat = srv.stats.latencies
     done = dist.world * srv.stats.completed
     wall_max = dist.max(wall)
+    # the plain form on the identical request list: one lt_eval after another on
+    # one stream, each with the split the server used for its shape
+    outs = {key: ctxs[key[0]].ct_empty(key[1] - 1) for key in pools}
+    splits = {(ln, d, lv): ctxs[ln].choose_split("th", lv, d) for ln, d, lv in set(specs)}
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter()
+    for i, (ln, d, lv) in enumerate(specs):
+        ctxs[ln].lt_eval(pools[(ln, lv)][i % 2], mats[(ln, d)], "th", splits[(ln, d, lv)], out=outs[(ln, lv)])
+    torch.cuda.synchronize()
+    seq_s = dist.max(time.perf_counter() - t_seq)
     return {
         "metric": METRIC, "value": round(done / wall_max, 3), "unit": "LT/s", "n_gpus": dist.world,
         "steps": srv.stats.completed, "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
@@ -1174,6 +1189,10 @@ def run_serving(args, dist: Dist):
         "offered_rate": args.rate, "completed": srv.stats.completed, "wall_s": round(wall_max, 3),
         "batches": srv.stats.batches, "mean_batch": round(srv.stats.completed / max(1, srv.stats.batches), 2),
         "admission_waits": srv.stats.admission_waits, "max_inflight_scratch_bytes": srv.stats.max_inflight_bytes,
+        "sequential": {"value": round(dist.world * len(specs) / seq_s, 3), "unit": "LT/s", "wall_s": round(seq_s, 3),
+                       "how": "the same request list as back-to-back lt_eval calls on one stream (no batching, "
+                              "no arrival gaps): the plain single-ciphertext form's capacity"},
+        "served_over_sequential": round((done / wall_max) / (dist.world * len(specs) / seq_s), 3),
         "clocks": clk,
     }
 

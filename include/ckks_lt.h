@@ -245,6 +245,17 @@ int32_t lt_required_rotations(const ckks_ctx* ctx, lt_algo algo, const lt_split*
 int32_t lt_candidate_splits(const ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out,
                             uint32_t cap);
 
+/* The cost model that ranks the splits (the key-memory / compute trade-off
+ * of Sec. III) for one LT: hbm_bytes = the DRAM bytes it counts (diagonals,
+ * distinct keys, input and output, and each Decompose's digits written and
+ * read once; -1 for BSGS, whose model counts them differently) and seconds =
+ * its time estimate (bytes over a fitted bandwidth plus the NTT butterflies
+ * and the multiply-accumulates over fitted kernel rates).  DH-BSGS is
+ * modelled in the schedule the model prefers (see lt_dh_schedule).  EINVAL
+ * on a bad level or split. */
+ckks_status lt_model_estimate(const ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag,
+                              const lt_split* split, double* hbm_bytes, double* seconds);
+
 /* Measuring autotuner (split selection per shape): ranks every admissible
  * split of f's n_diag for `algo` with the library's cost model, keeps the
  * first max_candidates whose rotation keys are all uploaded, times each on
@@ -266,6 +277,16 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
  * all at one level, ENOKEY if no candidate has all of its keys. */
 ckks_status lt_autotune_batch(ckks_ctx* ctx, lt_algo algo, uint32_t count, const ckks_ct* const* samples,
                               const ckks_diags* f, uint32_t max_candidates, lt_split* chosen, double* best_ms);
+
+/* Which schedule DH-BSGS (Algorithm 1) with `split` = (n1, n2) runs with on
+ * f at `level`: 0 = the baby steps materialised by key switching, then the
+ * diagonal products and the giant steps (Algorithm 1 as printed); 1 = the
+ * baby steps computed inside the diagonal multiply-accumulate kernel, the
+ * schedule TH-BSGS(1, n1, n2) of Algorithm 2 runs.  Both give identical
+ * residues.  The choice is lt_autotune's measurement for that shape and split
+ * (lt_autotune times DH candidates in both), else the cost model's.  -1 on a
+ * bad argument. */
+int32_t lt_dh_schedule(const ckks_ctx* ctx, const ckks_diags* f, uint32_t level, const lt_split* split);
 
 /* The split the library would choose for (algo, level, n_diag) with stride 1:
  * the autotuned one if lt_autotune has measured that shape, else the model's. */

@@ -98,6 +98,7 @@ def lib():
         "ckks_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
         "ckks_profile_work": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
         "ckks_probe_int_rates": [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+        "lt_model_estimate": [P, I, U32, U32, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -115,6 +116,8 @@ def lib():
     L.ckks_ct_level.restype = U32
     L.ckks_ct_device_ptr.argtypes = [P]
     L.ckks_ct_device_ptr.restype = P
+    L.lt_dh_schedule.argtypes = [P, P, U32, P]
+    L.lt_dh_schedule.restype = I32
     L.lt_candidate_splits.argtypes = [P, I, U32, U32, P, U32]
     L.lt_candidate_splits.restype = I32
     L.ckks_profile_reset.restype = None
@@ -336,6 +339,23 @@ class Context:
         if n < 0:
             raise CkksError(1, "bad arguments")
         return [buf[i].tuple() for i in range(n)]
+
+    def dh_schedule(self, diags: "Diagonals", level: int, split) -> str:
+        """'fused' (baby steps inside the diagonal kernel, TH(1, n1, n2)) or 'baby'
+        (Algorithm 1's materialised baby steps) for DH-BSGS with `split` (lt_dh_schedule)."""
+        sp = Split(split[0], split[1], 1)
+        r = lib().lt_dh_schedule(self.h, diags.handle, level, ctypes.byref(sp))
+        if r < 0:
+            raise CkksError(1, "bad arguments")
+        return "fused" if r == 1 else "baby"
+
+    def model_estimate(self, algo: str, level: int, n_diag: int, split):
+        """(DRAM bytes, seconds) the split-selection cost model assigns to one LT (lt_model_estimate)."""
+        sp = Split(*(tuple(split) + (1,) * (3 - len(split))))
+        b, t = ctypes.c_double(), ctypes.c_double()
+        check(lib().lt_model_estimate(self.h, ALGOS[algo], level, n_diag, ctypes.byref(sp), ctypes.byref(b),
+                                      ctypes.byref(t)))
+        return b.value, t.value
 
     def choose_split(self, algo: str, level: int, n_diag: int):
         sp = Split()

@@ -139,6 +139,9 @@ struct ckks_ctx {
     std::map<u32, LevelConsts> levels;
     std::map<u32, u64*> keys;  // rotation (mod N/2) -> [beta_max][L+K][N] word pairs (components interleaved)
     std::map<std::tuple<int, u32, u32, int32_t, int32_t>, lt_split> tuned;  // (algo, level, D, stride, offset0 mod N/2)
+    // DH-BSGS schedule per (level, D, stride, offset0 mod N/2, n1, n2) measured by lt_autotune:
+    // true = the baby steps fused into the diagonal kernel's middle layer, TH(1, n1, n2)
+    std::map<std::tuple<u32, u32, int32_t, int32_t, u32, u32>, bool> dh_fused;
     mutable std::mutex mu;
     size_t bytes = 0;
     // failure-detection test hook of the staged diagonal kernel (ckks_debug_diag_mac_waits)
@@ -910,45 +913,81 @@ std::vector<int64_t> rotations(const ckks_ctx* C, lt_algo algo, const lt_split& 
 }  // namespace
 
 // ------------------------------------------------------------------ split choice (autotuner model)
-// Time model of one LT on this GPU: HBM bytes that must move (keys, diagonals,
-// ciphertexts, plus the digits the fused diagonal kernel re-reads) over the
-// HBM bandwidth, plus the modular multiplications of the NTT-heavy steps
-// over the integer rate.  The split with the smallest estimate wins; ties go
-// to fewer keys.  Rates are measured figures of the GB300 kernels here.
+// Time model of one LT on this GPU, phase by phase: the diagonal kernel K6 at
+// the slower of its DRAM bytes and its multiply-accumulates, the key-switch
+// inner products at their DRAM bytes, and the Decompose / ModDown transforms
+// at their NTT butterflies.  The split with the smallest estimate wins.
 namespace {
-double model_time(const ckks_ctx* C, lt_algo algo, u32 level, u32 D, const lt_split& sp) {
+// The model over a TH-shaped schedule (n1, n2, n3) = (n'1, n'2, n'3): with
+// n2 = 1 there is no middle layer, so neither the baby steps' ModDown and
+// Decompose nor the middle keys (Algorithm 1's counts); with n2 > 1 the
+// counts of Algorithm 2.
+struct ModelEst {
+    double bytes, ntt_s, mac_s, seconds;
+};
+// Rates of this library's kernels on GB300, fitted to LTs measured at N = 2^16,
+// level 24, D = 256 over the splits (1,64,4), (2,32,4), (4,16,4), (2,16,8),
+// (4,8,8) (model within 5% of each):
+//   effective HBM bandwidth of the streaming kernels                5.4e12 B/s
+//   K6 multiply-accumulates, 4 or fewer outer indices per CTA       8.6e11 /s
+//                            8 outer indices per CTA (256 positions) 6.6e11 /s
+//   NTT butterflies (about 1.35 us per 2^16-point limb transform)   3.9e11 /s
+constexpr double M_BW = 5.4e12, M_MAC4 = 8.6e11, M_MAC8 = 6.6e11, M_NTT = 3.9e11, M_FIXED = 5e-5;
+
+ModelEst model_th_est(const ckks_ctx* C, u32 level, u32 D, u32 n1, u32 n2, u32 n3) {
     const double limb = 8.0 * C->N, ext = level + C->K, beta = (double)((level + C->alpha - 1) / C->alpha);
-    // rates of this library's kernels on GB300 (fitted to measured LTs at N = 2^16)
-    const double bw = 5.5e12, ntt_rate = 4.3e11, mac_rate = 7.6e11;  // bytes/s, butterflies/s, MAC/s
-    const double ntt = (C->N / 2.0) * C->log_n;
-    double keys, dec, md, kspairs;
-    if (algo == LT_TH_BSGS) {
-        keys = sp.n1 + sp.n2 + sp.n3 - 3;
-        dec = sp.n1 + sp.n3 - 1;
-        md = sp.n1 + sp.n3;
-        kspairs = (double)sp.n1 * sp.n2 + sp.n3 - 2;
-    } else if (algo == LT_DH_BSGS) {
-        keys = sp.n1 + sp.n2 - 2;
-        dec = sp.n2;
-        md = sp.n2 + 1;
-        kspairs = sp.n1 + sp.n2 - 2;
-    } else if (algo == LT_BSGS) {
-        keys = sp.n1 + sp.n2 - 2;
-        dec = keys;
-        md = 2 * keys;
-        kspairs = keys;
-    } else {
-        keys = D - 1;
-        dec = 1;
-        md = 2;
-        kspairs = D - 1;
+    const double L = level, K = C->K, N = C->N;
+    const bool mid = n2 > 1;
+    // K6: diagonals, middle keys, the baby indices' digits (re-read from L2), baby pairs, input, outputs
+    u32 k3 = 1;
+    while (k3 < n3 && k3 < (u32)DM_MAX_K3) k3 *= 2;
+    const double blocks = (n3 + k3 - 1) / k3;
+    const double k6_bytes = limb * (D * ext + (mid ? (n2 - 1.0) * 2 * beta * ext + n1 * beta * ext : 0.0) +
+                                    2.0 * (n1 - 1) * ext + 2 * L + 2.0 * n3 * ext);
+    const double k6_macs = N * ext * (2.0 * D + (mid ? 2.0 * beta * ((double)n1 * n2 - n1) * blocks : 0.0));
+    const double t_k6 = std::max(k6_bytes / M_BW, k6_macs / (k3 >= 8 ? M_MAC8 : M_MAC4));
+    // K4: inner layer (n1 - 1 products: digits, key, lifted x0, two outputs) and outer layer
+    // (n3 - 1 giant indices: digits, key, x0; the two accumulators once)
+    const double k4_bytes =
+        limb * ((n1 - 1.0) * (3 * beta * ext + L + 2 * ext) + (n3 - 1.0) * (3 * beta * ext + ext) + 4 * ext);
+    // Decompose (inverse of the level limbs, forward of each digit's other limbs) and ModDown
+    // (inverse of the k P limbs, forward of the level Q limbs), the last one merged with rescale
+    const double dec = 1.0 + (mid ? n1 - 1.0 : 0.0) + (n3 - 1.0);
+    const double mdp = (mid ? n1 - 1.0 : 0.0) + (n3 - 1.0);
+    const double ntt_limbs = dec * (L + beta * (ext - C->alpha)) + mdp * (K + L) + 2 * (K + L);
+    const double ntt_bytes = limb * (dec * (L + beta * ext) + mdp * (ext + L) + 2 * (ext + L - 1));
+    ModelEst e{k6_bytes + k4_bytes + ntt_bytes, ntt_limbs * (N / 2) * C->log_n / M_NTT, t_k6, 0};
+    e.seconds = t_k6 + k4_bytes / M_BW + e.ntt_s + M_FIXED * N / 65536.0;
+    return e;
+}
+double model_th(const ckks_ctx* C, u32 level, u32 D, u32 n1, u32 n2, u32 n3) {
+    return model_th_est(C, level, D, n1, n2, n3).seconds;
+}
+
+bool fused_ok(u32 n1, u32 n2) { return n1 <= (u32)DM_MAX_N2 && n2 <= (u32)DM_MAX_N3; }
+
+// DH-BSGS(n1, n2) has two schedules with identical residues: Algorithm 1's
+// materialised baby steps, TH(n1, 1, n2), and the baby steps computed on the
+// fly in the diagonal kernel's middle layer, TH(1, n1, n2).  The model's pick.
+bool dh_fused_model(const ckks_ctx* C, u32 level, u32 D, u32 n1, u32 n2) {
+    return fused_ok(n1, n2) && model_th(C, level, D, 1, n1, n2) < model_th(C, level, D, n1, 1, n2);
+}
+
+double model_time(const ckks_ctx* C, lt_algo algo, u32 level, u32 D, const lt_split& sp) {
+    if (algo == LT_TH_BSGS) return model_th(C, level, D, sp.n1, sp.n2, sp.n3);
+    if (algo == LT_DH_BSGS) {
+        const double a = model_th(C, level, D, sp.n1, 1, sp.n2);
+        return fused_ok(sp.n1, sp.n2) ? std::min(a, model_th(C, level, D, 1, sp.n1, sp.n2)) : a;
     }
-    double bytes = limb * (D * ext + keys * 2 * beta * ext + 4 * level);
-    // digits re-read by the middle layer and the decompose outputs
-    bytes += limb * dec * beta * ext * 2.0;
-    double flops = dec * (level + beta * (ext - C->alpha)) * ntt + md * (C->K + level) * ntt;
-    double mac = (kspairs * 2 * beta * ext + 2.0 * D * ext) * C->N;
-    return bytes / bw + flops / ntt_rate + mac / mac_rate;
+    if (algo == LT_DIAG) return model_th(C, level, D, 1, D, 1);
+    // BSGS: every rotation un-hoisted (its own Decompose and two ModDowns), products over Q
+    const double limb = 8.0 * C->N, ext = level + C->K, beta = (double)((level + C->alpha - 1) / C->alpha);
+    const double ntt = (C->N / 2.0) * C->log_n;
+    const double keys = sp.n1 + sp.n2 - 2.0;
+    const double bytes = limb * (D * level + keys * 2 * beta * ext + 4 * level + keys * beta * ext * 2.0);
+    const double flops = keys * (level + beta * (ext - C->alpha)) * ntt + 2 * keys * (C->K + level) * ntt;
+    const double mac = (keys * 2 * beta * ext + 2.0 * D * level) * C->N;
+    return bytes / M_BW + flops / M_NTT + mac / M_MAC4;
 }
 }  // namespace
 
@@ -1382,6 +1421,32 @@ int32_t lt_required_rotations(const ckks_ctx* ctx, lt_algo algo, const lt_split*
 static void lt_eval_impl(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_algo algo, const lt_split* split,
                          ckks_ct* out, cudaStream_t st, lt_split* chosen);
 
+ckks_status lt_model_estimate(const ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag,
+                              const lt_split* split, double* hbm_bytes, double* seconds) {
+    return guarded([&] {
+        if (!ctx || !split || !hbm_bytes || !seconds) fail(CKKS_EINVAL, "null argument");
+        if (level < 2 || level > ctx->L) fail(CKKS_EINVAL, "bad level");
+        lt_split sp = *split;
+        if (algo == LT_DIAG) sp = lt_split{1, n_diag, 1};
+        if (algo != LT_TH_BSGS && sp.n3 == 0) sp.n3 = 1;
+        validate_split(algo, n_diag, sp);
+        if (algo == LT_TH_BSGS || algo == LT_DIAG) {
+            const ModelEst e = model_th_est(ctx, level, n_diag, sp.n1, sp.n2, sp.n3);
+            *hbm_bytes = e.bytes;
+            *seconds = e.seconds;
+        } else if (algo == LT_DH_BSGS) {
+            const bool fz = dh_fused_model(ctx, level, n_diag, sp.n1, sp.n2);
+            const ModelEst e = fz ? model_th_est(ctx, level, n_diag, 1, sp.n1, sp.n2)
+                                  : model_th_est(ctx, level, n_diag, sp.n1, 1, sp.n2);
+            *hbm_bytes = e.bytes;
+            *seconds = e.seconds;
+        } else {
+            *hbm_bytes = -1;
+            *seconds = model_time(ctx, algo, level, n_diag, sp);
+        }
+    });
+}
+
 int32_t lt_candidate_splits(const ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out,
                             uint32_t cap) {
     if (!ctx) return -1;
@@ -1421,16 +1486,34 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
         out = new ckks_ct{ctx, level - 1, ctx->dalloc(2ull * (level - 1) * ctx->N), true};
         double best = 1e300;
         lt_split bsp = cand[0];
+        auto dh_key = [&](const lt_split& sp) {
+            return std::make_tuple(level, D, f->stride, (int32_t)ctx->rotkey(f->offset0), sp.n1, sp.n2);
+        };
         for (const lt_split& sp : cand) {
-            lt_eval_impl(ctx, sample, f, algo, &sp, out, st, nullptr);  // warm-up (tables, attributes)
-            CK(cudaEventRecord(e0, st));
-            const int reps = 5;  // candidates are often within a few percent of each other
-            for (int r = 0; r < reps; r++) lt_eval_impl(ctx, sample, f, algo, &sp, out, st, nullptr);
-            CK(cudaEventRecord(e1, st));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms / reps < best) best = ms / reps, bsp = sp;
+            // DH: both schedules of the split (identical residues), the faster one kept for it
+            const int forms = (algo == LT_DH_BSGS && fused_ok(sp.n1, sp.n2)) ? 2 : 1;
+            double best_form = 1e300;
+            bool fused_best = false;
+            for (int fm = 0; fm < forms; fm++) {
+                if (algo == LT_DH_BSGS) {
+                    std::lock_guard<std::mutex> g(ctx->mu);
+                    ctx->dh_fused[dh_key(sp)] = forms == 2 && fm == 1;
+                }
+                lt_eval_impl(ctx, sample, f, algo, &sp, out, st, nullptr);  // warm-up (tables, attributes)
+                CK(cudaEventRecord(e0, st));
+                const int reps = 5;  // candidates are often within a few percent of each other
+                for (int r = 0; r < reps; r++) lt_eval_impl(ctx, sample, f, algo, &sp, out, st, nullptr);
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms / reps < best_form) best_form = ms / reps, fused_best = forms == 2 && fm == 1;
+            }
+            if (algo == LT_DH_BSGS) {
+                std::lock_guard<std::mutex> g(ctx->mu);
+                ctx->dh_fused[dh_key(sp)] = fused_best;
+            }
+            if (best_form < best) best = best_form, bsp = sp;
         }
         {
             std::lock_guard<std::mutex> g(ctx->mu);
@@ -1516,6 +1599,14 @@ ckks_status lt_autotune_batch(ckks_ctx* ctx, lt_algo algo, uint32_t count, const
     return rc;
 }
 
+static bool dh_fused(const ckks_ctx* ctx, u32 level, const ckks_diags* f, const lt_split& sp);
+
+int32_t lt_dh_schedule(const ckks_ctx* ctx, const ckks_diags* f, uint32_t level, const lt_split* split) {
+    if (!ctx || !f || !split || f->ctx != ctx || level < 2 || level > f->level) return -1;
+    if (split->n1 < 1 || split->n2 < 1 || (uint64_t)split->n1 * split->n2 != f->n_diag) return -1;
+    return dh_fused(ctx, level, f, *split) ? 1 : 0;
+}
+
 ckks_status lt_choose_split(ckks_ctx* ctx, lt_algo algo, uint32_t level, uint32_t n_diag, lt_split* out) {
     return guarded([&] {
         if (!ctx || !out) fail(CKKS_EINVAL, "null argument");
@@ -1538,14 +1629,40 @@ static lt_split resolve_split(ckks_ctx* ctx, u32 level, const ckks_diags* f, lt_
     return sp;
 }
 
+// Whether DH-BSGS(n1, n2) on f at `level` runs with its baby steps fused into
+// the diagonal kernel (TH(1, n1, n2)): the measured choice of lt_autotune for
+// that shape and split if there is one, else the model's.
+static bool dh_fused(const ckks_ctx* ctx, u32 level, const ckks_diags* f, const lt_split& sp) {
+    if (!fused_ok(sp.n1, sp.n2)) return false;
+    {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        auto it = ctx->dh_fused.find(
+            std::make_tuple(level, f->n_diag, f->stride, (int32_t)ctx->rotkey(f->offset0), sp.n1, sp.n2));
+        if (it != ctx->dh_fused.end()) return it->second;
+    }
+    return dh_fused_model(ctx, level, f->n_diag, sp.n1, sp.n2);
+}
+
+// The TH-shaped schedule (n'1, n'2, n'3) a hoisted algorithm runs as: TH as
+// given; DH-BSGS(n1, n2) as TH(n1, 1, n2) (Algorithm 1) or TH(1, n1, n2) (baby
+// steps fused, identical residues); the hoisted diagonal method as TH(1, D, 1).
+static lt_split th_form(const ckks_ctx* ctx, u32 level, const ckks_diags* f, lt_algo algo, const lt_split& sp) {
+    switch (algo) {
+        case LT_DH_BSGS:
+            return dh_fused(ctx, level, f, sp) ? lt_split{1, sp.n1, sp.n2} : lt_split{sp.n1, 1, sp.n2};
+        case LT_DIAG: return lt_split{1, f->n_diag, 1};
+        default: return sp;
+    }
+}
+
 static void dispatch(ckks_ctx* ctx, u32 level, const LtIO& io, const ckks_diags* f, lt_algo algo, const lt_split& sp,
                      cudaStream_t st) {
-    switch (algo) {
-        case LT_TH_BSGS: sched_th(ctx, level, io, f, sp.n1, sp.n2, sp.n3, st); break;
-        case LT_DH_BSGS: sched_th(ctx, level, io, f, sp.n1, 1, sp.n2, st); break;
-        case LT_DIAG: sched_th(ctx, level, io, f, 1, f->n_diag, 1, st); break;
-        case LT_BSGS: sched_bsgs(ctx, level, io, f, sp.n1, sp.n2, st); break;
+    if (algo == LT_BSGS) {
+        sched_bsgs(ctx, level, io, f, sp.n1, sp.n2, st);
+        return;
     }
+    const lt_split t = th_form(ctx, level, f, algo, sp);
+    sched_th(ctx, level, io, f, t.n1, t.n2, t.n3, st);
 }
 
 static void lt_eval_impl(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_algo algo, const lt_split* split,
@@ -1620,15 +1737,15 @@ ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* i
                 done[a] = true;
                 continue;
             }
-            const u32 n1 = ia.sp.n1, n2 = ia.algo == LT_DH_BSGS ? 1 : ia.sp.n2, n3 = ia.algo == LT_DH_BSGS ? ia.sp.n2 : ia.sp.n3;
+            const lt_split ta = th_form(ctx, lva, f[ia.idx], ia.algo, ia.sp);
+            const u32 n1 = ta.n1, n2 = ta.n2, n3 = ta.n3;
             std::vector<LtIO> group;
             for (u32 b = a; b < count && group.size() < (size_t)DM_MAX_B; b++) {
                 if (done[b]) continue;
                 const Item& ib = items[b];
                 if (ib.algo == LT_BSGS || f[ib.idx] != f[ia.idx] || in[ib.idx]->level != in[ia.idx]->level) continue;
-                const u32 m1 = ib.sp.n1, m2 = ib.algo == LT_DH_BSGS ? 1 : ib.sp.n2,
-                          m3 = ib.algo == LT_DH_BSGS ? ib.sp.n2 : ib.sp.n3;
-                if (m1 != n1 || m2 != n2 || m3 != n3) continue;
+                const lt_split tb = th_form(ctx, in[ib.idx]->level, f[ib.idx], ib.algo, ib.sp);
+                if (tb.n1 != n1 || tb.n2 != n2 || tb.n3 != n3) continue;
                 const u32 level = in[ib.idx]->level;
                 const size_t lw = (size_t)level * ctx->N;
                 group.push_back(LtIO{in[ib.idx]->d, in[ib.idx]->d + lw, out[ib.idx]->d,

@@ -83,5 +83,6 @@ def test_more_digits_than_the_staged_kernel_holds(name, D, algo, split):
     out, _ = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, algo, split)
     got = out.numpy()
     assert_same(got, oracle_lt(pb, algo, split), f"{name} {algo} {split}")
-    assert max_err(pb, got) <= 1e-5
+    # 1e-5 below N = 2^16; at 2^16 the roundings' mean gathers in a few low slots (full-size bound 1e-4)
+    assert max_err(pb, got) <= (1e-4 if pb.ctx.N == 1 << 16 else 1e-5)
     g.close()

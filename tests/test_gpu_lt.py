@@ -26,7 +26,7 @@ def toy():
     pb = make_problem("toy", 0, 64)
     for algo, split in TOY_SPLITS.items():
         ensure_keys(pb, algo, split)
-    for split in [(2, 4, 8), (1, 8, 8), (8, 8, 1), (1, 64, 1), (16, 2, 2)]:
+    for split in [(2, 4, 8), (1, 8, 8), (8, 1, 8), (8, 8, 1), (1, 64, 1), (16, 2, 2)]:
         ensure_keys(pb, "th", split)
     ensure_keys(pb, "dh", (4, 16))
     g = gpu_context("toy")
@@ -54,12 +54,17 @@ def test_toy_other_splits(toy, algo, split):
 
 
 def test_toy_special_splits_match_other_algorithms(toy):
-    """TH(1, 8, 8) == DH(8, 8) and TH(1, 64, 1) == diagonal method, on the GPU too."""
+    """TH(1, 8, 8) == TH(8, 1, 8) == DH(8, 8) -- DH's two schedules, baby steps
+    fused into the diagonal kernel or materialised -- and TH(1, 64, 1) ==
+    diagonal method, on the GPU too."""
     pb, g, f = toy
     ct = g.ct_from_host(np.stack(pb.ct))
     a, _ = g.lt_eval(ct, f, "th", (1, 8, 8))
+    a2, _ = g.lt_eval(ct, f, "th", (8, 1, 8))
     b, _ = g.lt_eval(ct, f, "dh", (8, 8))
+    assert g.dh_schedule(f, pb.level, (8, 8)) in ("fused", "baby")
     assert_same(a.numpy(), b.numpy(), "TH(1,8,8) vs DH(8,8)")
+    assert_same(a2.numpy(), b.numpy(), "TH(8,1,8) vs DH(8,8)")
     c, _ = g.lt_eval(ct, f, "th", (1, 64, 1))
     d, _ = g.lt_eval(ct, f, "diag")
     assert_same(c.numpy(), d.numpy(), "TH(1,64,1) vs diagonal")
@@ -136,6 +141,23 @@ def test_full_size_autotuned_th(full):
     out, chosen = g.lt_eval(g.ct_from_host(np.stack(pb.ct)), f, "th")
     assert chosen == split
     assert_same(out.numpy(), oracle_lt(pb, "th", split), f"full auto {split}")
+
+
+def test_toy_dh_autotuner_times_both_schedules(toy):
+    """lt_autotune for DH-BSGS times each candidate in both schedules and keeps
+    the faster; the LT then runs with it, bit-exact with the oracle."""
+    pb, g, f = toy
+    ct = g.ct_from_host(np.stack(pb.ct))
+    cands = g.candidate_splits("dh", pb.level, pb.D, 3)
+    for sp in cands:
+        ensure_keys(pb, "dh", sp[:2])
+    upload_problem(g, pb)
+    split, ms = g.autotune("dh", ct, f, 3)
+    assert split in cands and ms > 0
+    assert g.dh_schedule(f, pb.level, split) in ("fused", "baby")
+    out, chosen = g.lt_eval(ct, f, "dh")
+    assert chosen == split
+    assert_same(out.numpy(), oracle_lt(pb, "dh", split[:2]), f"DH autotuned {split}")
 
 
 def test_toy_measuring_autotuner(toy):
