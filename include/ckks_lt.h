@@ -278,6 +278,18 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
 ckks_status lt_autotune_batch(ckks_ctx* ctx, lt_algo algo, uint32_t count, const ckks_ct* const* samples,
                               const ckks_diags* f, uint32_t max_candidates, lt_split* chosen, double* best_ms);
 
+/* The tile lt_autotune measured for the shape (algo, f, level) besides its
+ * split: outer rotation indices per CTA of the diagonal multiply-accumulate
+ * kernel (Alg. 2 lines 8-14) and positions per CTA, each 0 for the default
+ * (outer: the next power of two >= n'3, at most 8; positions: 512, or 256
+ * with 8 outer indices).  lt_autotune times the default, half the outer
+ * indices, and 256 positions (two CTAs per SM) for its chosen split, and
+ * lt_eval uses the fastest whenever it runs that split for that shape;
+ * results do not depend on the tile.  Returns 1 and writes the tile, 0 if
+ * the shape was not tuned, -1 on a null argument. */
+int32_t lt_tuned_tile(const ckks_ctx* ctx, lt_algo algo, const ckks_diags* f, uint32_t level, uint32_t* outer_per_cta,
+                      uint32_t* positions_per_cta);
+
 /* Which schedule DH-BSGS (Algorithm 1) with `split` = (n1, n2) runs with on
  * f at `level`: 0 = the baby steps materialised by key switching, then the
  * diagonal products and the giant steps (Algorithm 1 as printed); 1 = the
@@ -383,6 +395,14 @@ ckks_status ckks_selftest_bounded_wait(ckks_ctx* ctx, uint32_t limit_ms, void* s
  * Faults nothing.  Reset with (0, 0xFFFFFFFF).  Not for production use; it
  * changes the context like an upload (no evaluation call may overlap it). */
 ckks_status ckks_debug_diag_mac_waits(ckks_ctx* ctx, uint64_t wait_limit_ns, uint32_t starve_step);
+
+/* Test hook: every later LT on the context runs the diagonal kernel with this
+ * tile (see lt_tuned_tile; outer_per_cta 0 or a power of two up to 8, at
+ * most the default; positions_per_cta 0, 256 or 512), instead of the tuned or
+ * default one; (0, 0) restores the normal choice.  Results do not depend on
+ * the tile, which is what the test checks.  It changes the context like an
+ * upload (no evaluation call may overlap it). */
+ckks_status ckks_debug_diag_mac_tile(ckks_ctx* ctx, uint32_t outer_per_cta, uint32_t positions_per_cta);
 
 const char* ckks_last_error(void);
 size_t ckks_device_bytes_in_use(const ckks_ctx* ctx);

@@ -94,6 +94,7 @@ def lib():
         "lt_graph_destroy": [P],
         "ckks_selftest_bounded_wait": [P, U32, P],
         "ckks_debug_diag_mac_waits": [P, ctypes.c_uint64, U32],
+        "ckks_debug_diag_mac_tile": [P, U32, U32],
         "ckks_profile_enable": [ctypes.c_char_p, I],
         "ckks_profile_read": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)],
         "ckks_profile_work": [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -116,6 +117,8 @@ def lib():
     L.ckks_ct_level.restype = U32
     L.ckks_ct_device_ptr.argtypes = [P]
     L.ckks_ct_device_ptr.restype = P
+    L.lt_tuned_tile.argtypes = [P, I, P, U32, P, P]
+    L.lt_tuned_tile.restype = I32
     L.lt_dh_schedule.argtypes = [P, P, U32, P]
     L.lt_dh_schedule.restype = I32
     L.lt_candidate_splits.argtypes = [P, I, U32, U32, P, U32]
@@ -264,6 +267,10 @@ class Context:
         """Failure-detection test hook (ckks_debug_diag_mac_waits); (0, 0xFFFFFFFF) resets it."""
         check(lib().ckks_debug_diag_mac_waits(self.h, int(wait_limit_ns), int(starve_step)))
 
+    def debug_diag_mac_tile(self, outer_per_cta: int = 0, positions_per_cta: int = 0) -> None:
+        """Test hook (ckks_debug_diag_mac_tile): force the diagonal kernel's tile; (0, 0) resets."""
+        check(lib().ckks_debug_diag_mac_tile(self.h, int(outer_per_cta), int(positions_per_cta)))
+
     def bytes_in_use(self) -> int:
         return lib().ckks_device_bytes_in_use(self.h)
 
@@ -339,6 +346,15 @@ class Context:
         if n < 0:
             raise CkksError(1, "bad arguments")
         return [buf[i].tuple() for i in range(n)]
+
+    def tuned_tile(self, algo: str, diags: "Diagonals", level: int):
+        """(outer indices per CTA, positions per CTA) lt_autotune measured for the
+        shape (0 = default), or None if the shape was not tuned (lt_tuned_tile)."""
+        k3, run = ctypes.c_uint32(), ctypes.c_uint32()
+        r = lib().lt_tuned_tile(self.h, ALGOS[algo], diags.handle, level, ctypes.byref(k3), ctypes.byref(run))
+        if r < 0:
+            raise CkksError(1, "bad arguments")
+        return (k3.value, run.value) if r == 1 else None
 
     def dh_schedule(self, diags: "Diagonals", level: int, split) -> str:
         """'fused' (baby steps inside the diagonal kernel, TH(1, n1, n2)) or 'baby'

@@ -142,11 +142,14 @@ struct ckks_ctx {
     // DH-BSGS schedule per (level, D, stride, offset0 mod N/2, n1, n2) measured by lt_autotune:
     // true = the baby steps fused into the diagonal kernel's middle layer, TH(1, n1, n2)
     std::map<std::tuple<u32, u32, int32_t, int32_t, u32, u32>, bool> dh_fused;
+    // the diagonal kernel's tile measured by lt_autotune for a shape's tuned split (same key as `tuned`)
+    std::map<std::tuple<int, u32, u32, int32_t, int32_t>, std::pair<u32, u32>> tuned_tile;
     mutable std::mutex mu;
     size_t bytes = 0;
     // failure-detection test hook of the staged diagonal kernel (ckks_debug_diag_mac_waits)
     u64 dbg_wait_ns = 0;
     u32 dbg_starve_step = ~0u;
+    u32 dbg_tile_k3 = 0, dbg_tile_run = 0;  // forced diagonal-kernel tile (ckks_debug_diag_mac_tile)
     // fork/join lanes of lt_eval_batch: independent groups run on the caller's
     // stream and up to FORK_LANES - 1 more, so that one group's NTT-bound
     // phases overlap another's HBM-bound diagonal multiply-accumulate
@@ -490,9 +493,16 @@ void op_add_gather(ckks_ctx* C, u32 nlimbs, u32 level, const u64* a, const u64* 
     launch_add_gather((const ModC*)C->d_mods.p, j.data(), (int)nlimbs, gal, acc, C->log_n, st);
 }
 
-DiagMacArgs dm_base(ckks_ctx* C, u32 level, bool with_p, const ckks_diags* f) {
+// Tile of the diagonal kernel (0 = default; see DiagMacArgs).
+struct K6Tile {
+    u32 k3 = 0, run = 0;
+};
+
+DiagMacArgs dm_base(ckks_ctx* C, u32 level, bool with_p, const ckks_diags* f, K6Tile tile = K6Tile{}) {
     DiagMacArgs a;
     memset(&a, 0, sizeof(a));
+    a.tile_k3 = tile.k3;
+    a.tile_run = tile.run;
     a.mods = (const ModC*)C->d_mods.p;
     a.lift_c = C->d_lift.p;
     a.lift_sh = C->d_lift_sh.p;
@@ -546,7 +556,8 @@ OuterLayer outer_layer(const ckks_ctx* C, const ckks_diags* f, int64_t step, u32
 // is the case n1 = 1 with (n2, n3) = (n1, n2) of Algorithm 1, and the hoisted
 // diagonal method the case (1, D, 1): the three share this schedule and give
 // identical residues for those splits.
-void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 n2, u32 n3, cudaStream_t st) {
+void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 n2, u32 n3, cudaStream_t st,
+              K6Tile tile = K6Tile{}) {
     const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
     const int64_t s = f->stride;
     Arena ar(st, N);
@@ -574,7 +585,7 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
         op_moddown_batch(C, level, bs, tq, Y, st);
         op_decompose_batch(C, level, tqc, 0, dg, Y, st);
     }
-    DiagMacArgs a = dm_base(C, level, true, f);
+    DiagMacArgs a = dm_base(C, level, true, f, tile);
     a.n1 = n1;
     a.n2 = n2;
     a.n3 = n3;
@@ -656,7 +667,7 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
 // that each diagonal and key word is fetched from HBM once for the batch.
 // The results are identical to per-ciphertext sched_th.
 void sched_th_batch(ckks_ctx* C, u32 level, const std::vector<LtIO>& ios, const ckks_diags* f, u32 n1, u32 n2,
-                    u32 n3, cudaStream_t st) {
+                    u32 n3, cudaStream_t st, K6Tile tile = K6Tile{}) {
     const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
     const u32 nbat = (u32)ios.size();
     const size_t dig = (size_t)beta * ext;  // limbs of one digit set
@@ -714,7 +725,7 @@ void sched_th_batch(ckks_ctx* C, u32 level, const std::vector<LtIO>& ios, const 
         op_moddown_batch(C, level, bs, tq, Y, st);
         op_decompose_batch(C, level, tqc, 0, dg, Y, st);
     }
-    DiagMacArgs a = dm_base(C, level, true, f);
+    DiagMacArgs a = dm_base(C, level, true, f, tile);
     a.n1 = n1;
     a.n2 = n2;
     a.n3 = n3;
@@ -806,7 +817,8 @@ void sched_th_batch(ckks_ctx* C, u32 level, const std::vector<LtIO>& ios, const 
 
 // BSGS, Eq. (5): un-hoisted rotations (each with its own Decompose of the
 // rotated c1 and two ModDowns), products over Q, plain rescale at the end.
-void sched_bsgs(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 n2, cudaStream_t st) {
+void sched_bsgs(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 n2, cudaStream_t st,
+                K6Tile tile = K6Tile{}) {
     const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
     const int64_t s = f->stride;
     Arena ar(st, N);
@@ -829,7 +841,7 @@ void sched_bsgs(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u3
             op_moddown(C, level, X1, o1, Y, st);
         }
     };
-    DiagMacArgs a = dm_base(C, level, false, f);
+    DiagMacArgs a = dm_base(C, level, false, f, tile);
     a.n1 = n1;
     a.n2 = 1;
     a.n3 = n2;
@@ -1071,6 +1083,18 @@ ckks_status ckks_debug_diag_mac_waits(ckks_ctx* ctx, uint64_t wait_limit_ns, uin
         if (wait_limit_ns > 5000000000ull) fail(CKKS_EINVAL, "wait limit above 5 s");
         ctx->dbg_wait_ns = wait_limit_ns;
         ctx->dbg_starve_step = starve_step;
+    });
+}
+
+ckks_status ckks_debug_diag_mac_tile(ckks_ctx* ctx, uint32_t outer_per_cta, uint32_t positions_per_cta) {
+    return guarded([&] {
+        if (!ctx) fail(CKKS_EINVAL, "null argument");
+        if (outer_per_cta & (outer_per_cta - 1) || outer_per_cta > (u32)DM_MAX_K3)
+            fail(CKKS_EINVAL, "outer indices per CTA: 0 or a power of two up to 8");
+        if (positions_per_cta != 0 && positions_per_cta != 256 && positions_per_cta != 512)
+            fail(CKKS_EINVAL, "positions per CTA: 0, 256 or 512");
+        ctx->dbg_tile_k3 = outer_per_cta;
+        ctx->dbg_tile_run = positions_per_cta == 512 ? 0 : positions_per_cta;
     });
 }
 
@@ -1460,6 +1484,8 @@ int32_t lt_candidate_splits(const ckks_ctx* ctx, lt_algo algo, uint32_t level, u
     return (int32_t)n;
 }
 
+static lt_split th_form(const ckks_ctx* ctx, u32 level, const ckks_diags* f, lt_algo algo, const lt_split& sp);
+
 ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, const ckks_diags* f,
                         uint32_t max_candidates, lt_split* chosen, double* best_ms) {
     cudaStream_t st = nullptr;
@@ -1515,9 +1541,40 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
             }
             if (best_form < best) best = best_form, bsp = sp;
         }
+        const auto key = std::make_tuple((int)algo, level, D, f->stride, (int32_t)ctx->rotkey(f->offset0));
         {
             std::lock_guard<std::mutex> g(ctx->mu);
-            ctx->tuned[std::make_tuple((int)algo, level, D, f->stride, (int32_t)ctx->rotkey(f->offset0))] = bsp;
+            ctx->tuned[key] = bsp;
+            ctx->tuned_tile[key] = {0u, 0u};
+        }
+        // the diagonal kernel's tile for the chosen split: fewer outer indices per CTA
+        // (half the default), and 256 positions per CTA with two CTAs per SM
+        if (algo != LT_BSGS) {
+            const lt_split t = th_form(ctx, level, f, algo, bsp);
+            u32 k3 = 1;
+            while (k3 < t.n3 && k3 < (u32)DM_MAX_K3) k3 *= 2;
+            std::vector<std::pair<u32, u32>> tiles;
+            if (k3 >= 2) tiles.push_back({k3 / 2, 0u});
+            if (k3 < (u32)DM_MAX_K3) tiles.push_back({0u, 256u});
+            if (k3 >= 2 && k3 / 2 < (u32)DM_MAX_K3) tiles.push_back({k3 / 2, 256u});
+            std::pair<u32, u32> btile{0u, 0u};
+            for (const auto& tl : tiles) {
+                {
+                    std::lock_guard<std::mutex> g(ctx->mu);
+                    ctx->tuned_tile[key] = tl;
+                }
+                lt_eval_impl(ctx, sample, f, algo, &bsp, out, st, nullptr);
+                CK(cudaEventRecord(e0, st));
+                const int reps = 5;
+                for (int r = 0; r < reps; r++) lt_eval_impl(ctx, sample, f, algo, &bsp, out, st, nullptr);
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms / reps < best) best = ms / reps, btile = tl;
+            }
+            std::lock_guard<std::mutex> g(ctx->mu);
+            ctx->tuned_tile[key] = btile;
         }
         if (chosen) *chosen = bsp;
         if (best_ms) *best_ms = best;
@@ -1601,6 +1658,18 @@ ckks_status lt_autotune_batch(ckks_ctx* ctx, lt_algo algo, uint32_t count, const
 
 static bool dh_fused(const ckks_ctx* ctx, u32 level, const ckks_diags* f, const lt_split& sp);
 
+int32_t lt_tuned_tile(const ckks_ctx* ctx, lt_algo algo, const ckks_diags* f, uint32_t level, uint32_t* outer_per_cta,
+                      uint32_t* positions_per_cta) {
+    if (!ctx || !f || !outer_per_cta || !positions_per_cta) return -1;
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto tt = ctx->tuned_tile.find(
+        std::make_tuple((int)algo, level, f->n_diag, f->stride, (int32_t)ctx->rotkey(f->offset0)));
+    if (tt == ctx->tuned_tile.end()) return 0;
+    *outer_per_cta = tt->second.first;
+    *positions_per_cta = tt->second.second;
+    return 1;
+}
+
 int32_t lt_dh_schedule(const ckks_ctx* ctx, const ckks_diags* f, uint32_t level, const lt_split* split) {
     if (!ctx || !f || !split || f->ctx != ctx || level < 2 || level > f->level) return -1;
     if (split->n1 < 1 || split->n2 < 1 || (uint64_t)split->n1 * split->n2 != f->n_diag) return -1;
@@ -1655,14 +1724,29 @@ static lt_split th_form(const ckks_ctx* ctx, u32 level, const ckks_diags* f, lt_
     }
 }
 
+// The diagonal kernel's tile for an LT: the one lt_autotune measured for the
+// shape when `sp` is the shape's tuned split, else the default.
+static K6Tile tile_for(const ckks_ctx* ctx, u32 level, const ckks_diags* f, lt_algo algo, const lt_split& sp) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    if (ctx->dbg_tile_k3 || ctx->dbg_tile_run) return K6Tile{ctx->dbg_tile_k3, ctx->dbg_tile_run};
+    const auto key = std::make_tuple((int)algo, level, f->n_diag, f->stride, (int32_t)ctx->rotkey(f->offset0));
+    auto it = ctx->tuned.find(key);
+    auto tt = ctx->tuned_tile.find(key);
+    if (it == ctx->tuned.end() || tt == ctx->tuned_tile.end()) return K6Tile{};
+    const lt_split& t = it->second;
+    if (t.n1 != sp.n1 || t.n2 != sp.n2 || (algo == LT_TH_BSGS && t.n3 != sp.n3)) return K6Tile{};
+    return K6Tile{tt->second.first, tt->second.second};
+}
+
 static void dispatch(ckks_ctx* ctx, u32 level, const LtIO& io, const ckks_diags* f, lt_algo algo, const lt_split& sp,
                      cudaStream_t st) {
+    const K6Tile tile = tile_for(ctx, level, f, algo, sp);
     if (algo == LT_BSGS) {
-        sched_bsgs(ctx, level, io, f, sp.n1, sp.n2, st);
+        sched_bsgs(ctx, level, io, f, sp.n1, sp.n2, st, tile);
         return;
     }
     const lt_split t = th_form(ctx, level, f, algo, sp);
-    sched_th(ctx, level, io, f, t.n1, t.n2, t.n3, st);
+    sched_th(ctx, level, io, f, t.n1, t.n2, t.n3, st, tile);
 }
 
 static void lt_eval_impl(ckks_ctx* ctx, const ckks_ct* in, const ckks_diags* f, lt_algo algo, const lt_split* split,
@@ -1753,8 +1837,9 @@ ckks_status lt_eval_batch(ckks_ctx* ctx, uint32_t count, const ckks_ct* const* i
                 done[b] = true;
             }
             const ckks_diags* fa = f[ia.idx];
+            const K6Tile tile = tile_for(ctx, lva, fa, ia.algo, ia.sp);
             units.push_back(Unit{one * group.size(), [=](cudaStream_t s) {
-                                     sched_th_batch(ctx, lva, group, fa, n1, n2, n3, s);
+                                     sched_th_batch(ctx, lva, group, fa, n1, n2, n3, s, tile);
                                  }});
         }
         if (units.size() <= 1) {

@@ -149,6 +149,10 @@ struct DiagMacArgs {
     // The drain of copies in flight always keeps the default limit.
     u64 wait_ns;
     u32 starve_step;
+    // Tile (0 = default): outer indices per CTA (a power of two below the
+    // default, which is the next power of two >= n3, at most 8) and positions
+    // per CTA (256 = two CTAs per SM).  Results do not depend on it.
+    u32 tile_k3, tile_run;
     // Batch of ciphertexts sharing the diagonals and keys: ciphertext b uses
     // c0[b], c1[b] as its lifted inputs and A[i] + b*bs_ab, B[i] + b*bs_ab,
     // Dg[i] + b*bs_dg, U0/U1[k] + b*bs_u for the rest.  CTAs of the same

@@ -570,8 +570,8 @@ struct WsLayout {
     static constexpr size_t bytes(u32 n2) { return 8ull * STAGE * NS + ((4ull * n2 + 15) & ~15ull); }
 };
 
-template <int K3, int RUN, int NS, int BETA>
-__global__ void __launch_bounds__(RUN + 32, 1) k_diag_mac_ws(const __grid_constant__ DiagMacArgs a) {
+template <int K3, int RUN, int NS, int BETA, int MINB>
+__global__ void __launch_bounds__(RUN + 32, MINB) k_diag_mac_ws(const __grid_constant__ DiagMacArgs a) {
     using LY = WsLayout<K3, RUN, NS, BETA>;
     constexpr u32 NT = RUN + 32;  // threads of the CTA
     constexpr u32 RB = RUN * 8;   // bytes per run
@@ -838,7 +838,7 @@ bool try_staged(const DiagMacArgs& a, cudaStream_t st) {
     return true;
 }
 
-template <int K3, int RUN, int NS, int BETA>
+template <int K3, int RUN, int NS, int BETA, int MINB = 1>
 bool try_ws(const DiagMacArgs& a, cudaStream_t st) {
     using LY = WsLayout<K3, RUN, NS, BETA>;
     const u32 beta = a.n2 > 1 ? a.beta : 0;
@@ -854,8 +854,8 @@ bool try_ws(const DiagMacArgs& a, cudaStream_t st) {
     const uint64_t bit = 1ull << dev;
     if (attr_bad.load(std::memory_order_relaxed) & bit) return false;
     if (!(attr_set.load(std::memory_order_acquire) & bit)) {
-        if (cudaFuncSetAttribute(k_diag_mac_ws<K3, RUN, NS, BETA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)DM_SMEM_MAX) != cudaSuccess) {
+        if (cudaFuncSetAttribute(k_diag_mac_ws<K3, RUN, NS, BETA, MINB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DM_SMEM_MAX) != cudaSuccess) {
             cudaGetLastError();
             attr_bad.fetch_or(bit, std::memory_order_relaxed);
             return false;
@@ -863,7 +863,7 @@ bool try_ws(const DiagMacArgs& a, cudaStream_t st) {
         attr_set.fetch_or(bit, std::memory_order_release);
     }
     const dim3 grid((N / RUN) * a.batch, a.ext, (a.n3 + K3 - 1) / K3);
-    k_diag_mac_ws<K3, RUN, NS, BETA><<<grid, RUN + 32, sm, st>>>(a);
+    k_diag_mac_ws<K3, RUN, NS, BETA, MINB><<<grid, RUN + 32, sm, st>>>(a);
     return true;
 }
 
@@ -877,13 +877,24 @@ static int k6_form() {
     return f;
 }
 
+// Tile of the warp-specialised K6: positions per CTA.  512 (one CTA per SM)
+// by default, 256 with eight outer accumulators per thread (register budget);
+// tile_run = 256 asks for 256 positions with two CTAs per SM where the
+// registers allow it (four or fewer outer indices per CTA).
+template <int K3>
+bool launch_ws(const DiagMacArgs& a, cudaStream_t st) {
+    const bool mid = a.n2 > 1;
+    if constexpr (K3 >= 8) {
+        return mid ? try_ws<K3, 256, 2, 6>(a, st) : try_ws<K3, 256, 4, 0>(a, st);
+    } else {
+        if (a.tile_run == 256) return mid ? try_ws<K3, 256, 2, 6, 2>(a, st) : try_ws<K3, 256, 4, 0, 2>(a, st);
+        return mid ? try_ws<K3, 512, 2, 6>(a, st) : try_ws<K3, 512, 4, 0>(a, st);
+    }
+}
+
 template <int K3>
 bool launch_staged(const DiagMacArgs& a, cudaStream_t st) {
-    if (k6_form() == 0) {
-        // 512 positions per CTA; 256 with eight outer accumulators per thread (register budget)
-        constexpr int RUN = K3 >= 8 ? 256 : 512;
-        if (a.n2 > 1 ? try_ws<K3, RUN, 2, 6>(a, st) : try_ws<K3, RUN, 4, 0>(a, st)) return true;
-    }
+    if (k6_form() == 0 && launch_ws<K3>(a, st)) return true;
     return try_staged<K3, 512, 4, 6>(a, st) || try_staged<K3, 512, 3, 6>(a, st) || try_staged<K3, 256, 4, 6>(a, st);
 }
 
@@ -947,6 +958,8 @@ void launch_diag_mac(const DiagMacArgs& a, cudaStream_t st) {
     const u32 N = 1u << a.log_n;
     u32 k3 = 1;
     while (k3 < a.n3 && k3 < (u32)DM_MAX_K3) k3 *= 2;
+    // a tile with fewer outer indices per CTA (more CTAs along z, each redoing the middle layer)
+    if (a.tile_k3 && a.tile_k3 < k3 && !(a.tile_k3 & (a.tile_k3 - 1))) k3 = a.tile_k3;
     const dim3 grid(((N + THREADS - 1) / THREADS) * a.batch, a.ext, (a.n3 + k3 - 1) / k3);
     // multiply-accumulates: two per diagonal product (c0, c1), and the middle
     // layer's 2 beta per step with j > 0, once per block of k3 outer indices

@@ -160,6 +160,26 @@ def test_toy_dh_autotuner_times_both_schedules(toy):
     assert_same(out.numpy(), oracle_lt(pb, "dh", split[:2]), f"DH autotuned {split}")
 
 
+@pytest.mark.parametrize("split", [(4, 4, 4), (2, 4, 8), (1, 8, 8)])
+def test_toy_every_diagonal_kernel_tile(toy, split):
+    """Every tile of the diagonal kernel (outer indices per CTA below the
+    default, 256 positions with two CTAs per SM) gives the oracle's residues."""
+    pb, g, f = toy
+    ct = g.ct_from_host(np.stack(pb.ct))
+    want = oracle_lt(pb, "th", split)
+    k3 = 1
+    while k3 < split[2] and k3 < 8:
+        k3 *= 2
+    try:
+        for outer in sorted({0, k3 // 2 or 0, 1}):
+            for pos in (0, 256):
+                g.debug_diag_mac_tile(outer, pos)
+                out, _ = g.lt_eval(ct, f, "th", split)
+                assert_same(out.numpy(), want, f"toy {split} tile ({outer}, {pos})")
+    finally:
+        g.debug_diag_mac_tile(0, 0)
+
+
 def test_toy_measuring_autotuner(toy):
     """lt_autotune times the model's candidates that have keys, records the
     fastest, and lt_eval without a split then uses it (bit-exact with the oracle)."""
@@ -172,6 +192,7 @@ def test_toy_measuring_autotuner(toy):
     upload_problem(g, pb)
     split, ms = g.autotune("th", ct, f, 4)
     assert split in cands and ms > 0
+    assert g.tuned_tile("th", f, pb.level) is not None
     out, chosen = g.lt_eval(ct, f, "th")
     assert chosen == split
     assert_same(out.numpy(), oracle_lt(pb, "th", split), f"autotuned {split}")
