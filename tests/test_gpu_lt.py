@@ -163,7 +163,7 @@ def test_toy_dh_autotuner_times_both_schedules(toy):
 @pytest.mark.parametrize("split", [(4, 4, 4), (2, 4, 8), (1, 8, 8)])
 def test_toy_every_diagonal_kernel_tile(toy, split):
     """Every tile of the diagonal kernel (outer indices per CTA below the
-    default, 256 positions with two CTAs per SM) gives the oracle's residues."""
+    default, 512 positions with one CTA per SM) gives the oracle's residues."""
     pb, g, f = toy
     ct = g.ct_from_host(np.stack(pb.ct))
     want = oracle_lt(pb, "th", split)
@@ -172,7 +172,7 @@ def test_toy_every_diagonal_kernel_tile(toy, split):
         k3 *= 2
     try:
         for outer in sorted({0, k3 // 2 or 0, 1}):
-            for pos in (0, 256):
+            for pos in (0, 512):
                 g.debug_diag_mac_tile(outer, pos)
                 out, _ = g.lt_eval(ct, f, "th", split)
                 assert_same(out.numpy(), want, f"toy {split} tile ({outer}, {pos})")
@@ -196,3 +196,16 @@ def test_toy_measuring_autotuner(toy):
     out, chosen = g.lt_eval(ct, f, "th")
     assert chosen == split
     assert_same(out.numpy(), oracle_lt(pb, "th", split), f"autotuned {split}")
+
+
+def test_cost_model_is_the_one_restated_on_cpu():
+    """lt_model_estimate computes exactly the model tests/test_cost_model.py
+    restates and checks against measured DRAM bytes and LT times."""
+    from test_cost_model import model
+
+    g = gpu_context("n16")
+    for sp in [(1, 64, 4), (2, 32, 4), (4, 16, 4), (4, 8, 8), (2, 16, 8), (1, 32, 8)]:
+        b, s = g.model_estimate("th", 24, 256, sp)
+        wb, ws = model(24, 256, *sp)
+        assert abs(b - wb) <= 1e-9 * wb and abs(s - ws) <= 1e-9 * ws, (sp, b, wb, s, ws)
+    g.close()
