@@ -570,6 +570,166 @@ struct WsLayout {
     static constexpr size_t bytes(u32 n2) { return 8ull * STAGE * NS + ((4ull * n2 + 15) & ~15ull); }
 };
 
+// What the compute threads of k_diag_mac_ws share.
+struct WsCtx {
+    const DiagMacArgs& a;
+    const u64* smem;
+    u64* full_bar;
+    u64* empty_bar;
+    volatile u32* abort;
+    u32 s, l, n1, n2, beta, k_first, k_count;
+    size_t tN, ou;
+    bool lift_limb, c0_lifted;
+    u64 lc, lsh;
+    ModC m;
+};
+
+template <bool SMALL>
+struct WsAcc;
+template <>
+struct WsAcc<true> {  // operands below 2^41: three-word sums (mac96)
+    U96 v;
+    __device__ __forceinline__ void zero() { v = U96{0, 0}; }
+    __device__ __forceinline__ void mac(u64 x, u64 y) { mac96(v, x, y); }
+    __device__ __forceinline__ void add(u64 x) { add96(v, x); }
+    __device__ __forceinline__ U128 wide() const { return U128{v.lo, v.hi}; }
+    __device__ __forceinline__ void set(u64 x) { v = U96{x, 0}; }
+};
+template <>
+struct WsAcc<false> {  // any residue below 2^60: four-word sums (mac128)
+    U128 v;
+    __device__ __forceinline__ void zero() { v = U128{0, 0}; }
+    __device__ __forceinline__ void mac(u64 x, u64 y) { mac128(v, x, y); }
+    __device__ __forceinline__ void add(u64 x) { add128(v, x); }
+    __device__ __forceinline__ U128 wide() const { return v; }
+    __device__ __forceinline__ void set(u64 x) { v = U128{x, 0}; }
+};
+
+// The compute threads' step loop of k_diag_mac_ws (see there) and the output.
+// SMALL (2^32 < q < 2^41, beta <= 8): every operand is below 2^41, the
+// middle-layer sum x = sum_b d_b k_b + A is below 2^85, and it is brought
+// into [0, 3q) (a fold below 2^64, then a quotient estimate with the 32-bit
+// mu = floor(2^64 / q)) so that 64 outer products with a word below q stay
+// below 2^96: mac96 throughout.  Otherwise 128-bit sums, reduced lazily.
+template <int K3, int RUN, int NS, int BETA, bool SMALL>
+__device__ __forceinline__ void ws_compute(const WsCtx& c) {
+    using LY = WsLayout<K3, RUN, NS, BETA>;
+    constexpr u32 FULL = 0xffffffffu;
+    const DiagMacArgs& a = c.a;
+    const u32 l = c.l, s = c.s, n1 = c.n1, n2 = c.n2, n1n2 = n1 * n2, beta = c.beta;
+    const ModC m = c.m;
+    const u64 wait_ns = a.wait_ns ? a.wait_ns : DM_WAIT_NS;
+    const bool fold = m.q < (1ull << 41) && beta <= 8;
+    const u64 c63 = fold ? (1ull << 63) % m.q : 0, c64 = fold ? (0 - m.q) % m.q : 0;  // 2^63, 2^64 mod q
+    const u32 mu32 = (u32)m.mu_hi;  // floor(2^64 / q) (SMALL: below 2^32)
+    u32 pd[K3];
+#pragma unroll
+    for (int kk = 0; kk < K3; kk++) {
+        const u32 kc = c.k_first + min((u32)kk, c.k_count - 1);
+        const u32 g = a.gal_diag[kc];
+        const u32 run = s / RUN;
+        const u32 hr = (g ? auto_src(run * RUN, g, a.log_n) : run * RUN) / RUN;
+        pd[kk] = (g ? auto_src(s, g, a.log_n) : s) - hr * RUN;
+    }
+    WsAcc<SMALL> acc0[K3], acc1[K3];
+#pragma unroll
+    for (int kk = 0; kk < K3; kk++) acc0[kk].zero(), acc1[kk].zero();
+    u32 terms = 0;
+    for (u32 it = 0; it < n1n2; it++) {
+        const u32 sidx = it % NS;
+        // the warp decides together, so that its lanes stay converged
+        if (!__all_sync(FULL, mbar_wait_abortable(&c.full_bar[sidx], (it / NS) & 1, wait_ns, c.abort))) {
+            *c.abort = 1u;
+            break;
+        }
+        const u32 j = n1 == 1 ? it : it / n1, i = n1 == 1 ? 0u : it % n1;
+        const bool lifted = (i == 0) && a.lift0;
+        const u64* st = c.smem + (size_t)sidx * LY::STAGE;
+        u64 av, bv;
+        if (j == 0) {
+            if (lifted) {
+                if (c.lift_limb) {
+                    const u64 x = st[LY::OFF_A + l];
+                    av = c.c0_lifted ? x : mul_shoup(x, c.lc, c.lsh, m.q);
+                    bv = mul_shoup(st[LY::OFF_B + l], c.lc, c.lsh, m.q);
+                } else {
+                    av = bv = 0;
+                }
+            } else {
+                av = st[LY::OFF_A + l];
+                bv = st[LY::OFF_B + l];
+            }
+        } else {
+            const u32 pm = auto_src(s, a.gal_mid[j], a.log_n) % RUN;
+            WsAcc<SMALL> x0, x1;
+            x0.zero();
+            x1.zero();
+            const ulonglong2* kp = (const ulonglong2*)(st + LY::OFF_KEY) + l;
+#pragma unroll
+            for (int b = 0; b < BETA; b++) {
+                if (b < (int)beta) {
+                    const u64 d = st[LY::OFF_DIG + b * RUN + pm];
+                    const ulonglong2 kv = kp[b * RUN];
+                    x0.mac(d, kv.x);
+                    x1.mac(d, kv.y);
+                }
+            }
+            if (lifted) {
+                if (c.lift_limb) {
+                    const u64 x = st[LY::OFF_A + pm];
+                    x0.add(c.c0_lifted ? x : mul_shoup(x, c.lc, c.lsh, m.q));
+                }
+            } else {
+                x0.add(st[LY::OFF_A + pm]);
+            }
+            // partial reductions feed the products (see k_diag_mac_staged)
+            const U128 w0 = x0.wide(), w1 = x1.wide();
+            if (fold) {
+                av = (w0.lo & ~(1ull << 63)) + ((w0.lo >> 63) ? c63 : 0) + w0.hi * c64;
+                bv = (w1.lo & ~(1ull << 63)) + ((w1.lo >> 63) ? c63 : 0) + w1.hi * c64;
+                if constexpr (SMALL) {  // below 2^64 -> [0, 3q)
+                    const u64 qa = ((u64)(u32)(av >> 32) * mu32 + __umulhi((u32)av, mu32)) >> 32;
+                    const u64 qb = ((u64)(u32)(bv >> 32) * mu32 + __umulhi((u32)bv, mu32)) >> 32;
+                    av -= qa * m.q;
+                    bv -= qb * m.q;
+                }
+            } else {
+                av = reduce128_lazy(w0, m);
+                bv = reduce128_lazy(w1, m);
+            }
+        }
+        u64 f[K3];
+#pragma unroll
+        for (int kk = 0; kk < K3; kk++) f[kk] = kk < (int)c.k_count ? st[kk * RUN + pd[kk]] : 0;
+        __syncwarp();
+        if ((l & 31) == 0) mbar_arrive(&c.empty_bar[sidx]);  // the warp has read stage sidx
+#pragma unroll
+        for (int kk = 0; kk < K3; kk++) {
+            if (kk < (int)c.k_count) {
+                acc0[kk].mac(av, f[kk]);
+                acc1[kk].mac(bv, f[kk]);
+            }
+        }
+        if (++terms == 64) {  // 64 products fit the accumulators (2^122 each, or 2^83 on the 96-bit path)
+            terms = 0;
+#pragma unroll
+            for (int kk = 0; kk < K3; kk++) {
+                acc0[kk].set(reduce128(acc0[kk].wide(), m));
+                acc1[kk].set(reduce128(acc1[kk].wide(), m));
+            }
+        }
+    }
+    nbar_sync(1, RUN + 32);  // every thread of the CTA reaches this once; then one decision for all
+    if (*c.abort) return;
+#pragma unroll
+    for (int kk = 0; kk < K3; kk++) {
+        if (kk < (int)c.k_count) {
+            a.U0[c.k_first + kk][c.ou + c.tN + s] = reduce128(acc0[kk].wide(), m);
+            a.U1[c.k_first + kk][c.ou + c.tN + s] = reduce128(acc1[kk].wide(), m);
+        }
+    }
+}
+
 template <int K3, int RUN, int NS, int BETA, int MINB>
 __global__ void __launch_bounds__(RUN + 32, MINB) k_diag_mac_ws(const __grid_constant__ DiagMacArgs a) {
     using LY = WsLayout<K3, RUN, NS, BETA>;
@@ -687,106 +847,12 @@ __global__ void __launch_bounds__(RUN + 32, MINB) k_diag_mac_ws(const __grid_con
 
     // ---------------------------------------------------------------- compute threads
     const u32 s = run * RUN + l;
-    const u64 wait_ns = a.wait_ns ? a.wait_ns : DM_WAIT_NS;
     const u64 lc = lift_limb ? a.lift_c[gmod] : 0, lsh = lift_limb ? a.lift_sh[gmod] : 0;
-    const bool fold = m.q < (1ull << 41) && beta <= 8;
-    const u64 c63 = fold ? (1ull << 63) % m.q : 0, c64 = fold ? (0 - m.q) % m.q : 0;  // 2^63, 2^64 mod q
-    u32 pd[K3];
-#pragma unroll
-    for (int kk = 0; kk < K3; kk++) {
-        const u32 kc = k_first + min((u32)kk, k_count - 1);
-        const u32 g = a.gal_diag[kc];
-        const u32 hr = (g ? auto_src(run * RUN, g, a.log_n) : run * RUN) / RUN;
-        pd[kk] = (g ? auto_src(s, g, a.log_n) : s) - hr * RUN;
-    }
-    U128 acc0[K3], acc1[K3];
-#pragma unroll
-    for (int kk = 0; kk < K3; kk++) acc0[kk] = acc1[kk] = U128{0, 0};
-    u32 terms = 0;
-    for (u32 it = 0; it < n1n2; it++) {
-        const u32 sidx = it % NS;
-        // the warp decides together, so that its lanes stay converged
-        if (!__all_sync(FULL, mbar_wait_abortable(&full_bar[sidx], (it / NS) & 1, wait_ns, abort))) {
-            *abort = 1u;
-            break;
-        }
-        const u32 j = n1 == 1 ? it : it / n1, i = n1 == 1 ? 0u : it % n1;
-        const bool lifted = (i == 0) && a.lift0;
-        const u64* st = smem + (size_t)sidx * LY::STAGE;
-        u64 av, bv;
-        if (j == 0) {
-            if (lifted) {
-                if (lift_limb) {
-                    const u64 x = st[LY::OFF_A + l];
-                    av = c0l ? x : mul_shoup(x, lc, lsh, m.q);
-                    bv = mul_shoup(st[LY::OFF_B + l], lc, lsh, m.q);
-                } else {
-                    av = bv = 0;
-                }
-            } else {
-                av = st[LY::OFF_A + l];
-                bv = st[LY::OFF_B + l];
-            }
-        } else {
-            const u32 pm = auto_src(s, a.gal_mid[j], a.log_n) % RUN;
-            U128 x0{0, 0}, x1{0, 0};
-            const ulonglong2* kp = (const ulonglong2*)(st + LY::OFF_KEY) + l;
-#pragma unroll
-            for (int b = 0; b < BETA; b++) {
-                if (b < (int)beta) {
-                    const u64 d = st[LY::OFF_DIG + b * RUN + pm];
-                    const ulonglong2 kv = kp[b * RUN];
-                    mac128(x0, d, kv.x);
-                    mac128(x1, d, kv.y);
-                }
-            }
-            if (lifted) {
-                if (lift_limb) {
-                    const u64 x = st[LY::OFF_A + pm];
-                    add128(x0, c0l ? x : mul_shoup(x, lc, lsh, m.q));
-                }
-            } else {
-                add128(x0, st[LY::OFF_A + pm]);
-            }
-            // partial reductions feed the products (see k_diag_mac_staged)
-            if (fold) {
-                av = (x0.lo & ~(1ull << 63)) + ((x0.lo >> 63) ? c63 : 0) + x0.hi * c64;
-                bv = (x1.lo & ~(1ull << 63)) + ((x1.lo >> 63) ? c63 : 0) + x1.hi * c64;
-            } else {
-                av = reduce128_lazy(x0, m);
-                bv = reduce128_lazy(x1, m);
-            }
-        }
-        u64 f[K3];
-#pragma unroll
-        for (int kk = 0; kk < K3; kk++) f[kk] = kk < (int)k_count ? st[kk * RUN + pd[kk]] : 0;
-        __syncwarp();
-        if ((l & 31) == 0) mbar_arrive(&empty_bar[sidx]);  // the warp has read stage sidx
-#pragma unroll
-        for (int kk = 0; kk < K3; kk++) {
-            if (kk < (int)k_count) {
-                mac128(acc0[kk], av, f[kk]);
-                mac128(acc1[kk], bv, f[kk]);
-            }
-        }
-        if (++terms == 64) {  // 64 products below 2^122 each fit the accumulators
-            terms = 0;
-#pragma unroll
-            for (int kk = 0; kk < K3; kk++) {
-                acc0[kk] = U128{reduce128(acc0[kk], m), 0};
-                acc1[kk] = U128{reduce128(acc1[kk], m), 0};
-            }
-        }
-    }
-    nbar_sync(1, NT);  // every thread of the CTA reaches this once; then one decision for all
-    if (*abort) return;
-#pragma unroll
-    for (int kk = 0; kk < K3; kk++) {
-        if (kk < (int)k_count) {
-            a.U0[k_first + kk][ou + tN + s] = reduce128(acc0[kk], m);
-            a.U1[k_first + kk][ou + tN + s] = reduce128(acc1[kk], m);
-        }
-    }
+    const WsCtx c{a, smem, full_bar, empty_bar, abort, s, l, n1, n2, beta, k_first, k_count, tN, ou, lift_limb,
+                  c0l != nullptr, lc, lsh, m};
+    // moduli 2^32 < q < 2^41 (every 40-bit prime): 96-bit accumulators; wider ones: 128-bit
+    if (m.q > (1ull << 32) && m.q < (1ull << 41) && beta <= 8) ws_compute<K3, RUN, NS, BETA, true>(c);
+    else ws_compute<K3, RUN, NS, BETA, false>(c);
 }
 
 // P x on the Q limbs (Alg. 2 line 2), for every polynomial of a batch.

@@ -67,6 +67,47 @@ __device__ __forceinline__ void mac128(U128& acc, u64 a, u64 b) {
         : "l"(a), "l"(b));
 }
 
+// A 96-bit accumulator (low 64 bits, high 32 bits) for products of operands
+// below 2^41.
+struct U96 {
+    u64 lo;
+    u32 hi;
+};
+
+// acc += a * b for a, b < 2^41; the caller keeps the sum below 2^96.  With
+// a = a1 2^32 + a0 and b = b1 2^32 + b0 (a1, b1 < 2^9), a1 b1 is below 2^18
+// and the high halves of a0 b1 and a1 b0 below 2^9, so the top word takes
+// them with no carry out of it: seven 32-bit multiply-adds along three short
+// carry chains instead of mac128's ten.
+__device__ __forceinline__ void mac96(U96& acc, u64 a, u64 b) {
+    asm("{\n\t.reg .u32 w0, w1, x0, x1, y0, y1;\n\t"
+        "mov.b64 {w0, w1}, %0;\n\t"
+        "mov.b64 {x0, x1}, %2;\n\t"
+        "mov.b64 {y0, y1}, %3;\n\t"
+        "mad.lo.cc.u32 w0, x0, y0, w0;\n\t"
+        "madc.hi.cc.u32 w1, x0, y0, w1;\n\t"
+        "madc.lo.u32 %1, x1, y1, %1;\n\t"
+        "mad.lo.cc.u32 w1, x0, y1, w1;\n\t"
+        "madc.hi.u32 %1, x0, y1, %1;\n\t"
+        "mad.lo.cc.u32 w1, x1, y0, w1;\n\t"
+        "madc.hi.u32 %1, x1, y0, %1;\n\t"
+        "mov.b64 %0, {w0, w1};\n\t}"
+        : "+l"(acc.lo), "+r"(acc.hi)
+        : "l"(a), "l"(b));
+}
+
+__device__ __forceinline__ void add96(U96& acc, u64 v) {
+    asm("{\n\t.reg .u32 w0, w1, v0, v1;\n\t"
+        "mov.b64 {w0, w1}, %0;\n\t"
+        "mov.b64 {v0, v1}, %2;\n\t"
+        "add.cc.u32 w0, w0, v0;\n\t"
+        "addc.cc.u32 w1, w1, v1;\n\t"
+        "addc.u32 %1, %1, 0;\n\t"
+        "mov.b64 %0, {w0, w1};\n\t}"
+        : "+l"(acc.lo), "+r"(acc.hi)
+        : "l"(v));
+}
+
 __device__ __forceinline__ void add128(U128& acc, u64 v) {
     asm("add.cc.u64 %0, %0, %2;\n\t"
         "addc.u64 %1, %1, 0;"

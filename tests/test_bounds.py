@@ -104,3 +104,74 @@ def test_lazy_barrett_128(q):
         qe = (x_hi * mu_hi + ((x_hi * mu_lo) >> 64) + ((x_lo * mu_hi) >> 64)) & M64
         r = (x_lo - qe * q) & M64
         assert r % q == x % q and 0 <= r < 4 * q
+
+
+# ------------------------------------------------------------------ 96-bit multiply-accumulate (K6, q < 2^41)
+M32 = (1 << 32) - 1
+
+
+def mac96(lo, hi, a, b):
+    """The seven 32-bit multiply-adds of modarith.cuh's mac96 with their carry
+    flag, word for word: (lo, hi) += a b."""
+    w0, w1 = lo & M32, lo >> 32
+    x0, x1, y0, y1 = a & M32, a >> 32, b & M32, b >> 32
+
+    def add(dst, v, cin):  # 32-bit add with carry in; (result, carry out)
+        s = dst + v + cin
+        return s & M32, s >> 32
+
+    w0, c = add(w0, (x0 * y0) & M32, 0)               # mad.lo.cc
+    w1, c = add(w1, (x0 * y0) >> 32, c)               # madc.hi.cc
+    hi = (hi + ((x1 * y1) & M32) + c) & M32           # madc.lo (no carry out)
+    w1, c = add(w1, (x0 * y1) & M32, 0)               # mad.lo.cc
+    hi = (hi + ((x0 * y1) >> 32) + c) & M32           # madc.hi
+    w1, c = add(w1, (x1 * y0) & M32, 0)               # mad.lo.cc
+    hi = (hi + ((x1 * y0) >> 32) + c) & M32           # madc.hi
+    return w0 | (w1 << 32), hi
+
+
+def small_moduli():
+    """The moduli that take K6's 96-bit path: 2^32 < q < 2^41 (mu = floor(2^64 / q) fits 32 bits)."""
+    out = [q for q in MODULI if (1 << 32) < q < (1 << 41)]
+    assert out
+    return out
+
+
+def test_mac96_is_exact_below_2_96():
+    """For operands below 2^41 the three-word sum is the exact integer sum as
+    long as it stays below 2^96 -- the middle layer's 6 products plus A, and
+    64 outer products of a word below 3q with one below q."""
+    for q in small_moduli():
+        ops = [0, 1, q - 1, (1 << 41) - 1] + [RNG.randrange(q) for _ in range(60)]
+        for terms in (7, 64):
+            lo = hi = 0
+            exact = 0
+            for t in range(terms):
+                a = ops[(t * 7) % len(ops)] if t % 5 else (1 << 41) - 1
+                b = ops[(t * 13 + 3) % len(ops)]
+                lo, hi = mac96(lo, hi, a, b)
+                exact += a * b
+            assert exact < 1 << 96
+            assert lo | (hi << 64) == exact
+
+
+def test_middle_sum_reduction_for_the_96_bit_products():
+    """K6's reduction of a middle-layer sum x < 2^85 for the 96-bit outer
+    products: the fold to below 2^64, then the quotient estimate
+    ((a1 mu + hi(a0 mu)) >> 32), mu = floor(2^64 / q), leaves a word in
+    [0, 3q) congruent to x, and 64 of its products with a word below q stay
+    below 2^96."""
+    for q in small_moduli():
+        mu = (1 << 64) // q
+        assert mu < 1 << 32
+        c63, c64 = (1 << 63) % q, (1 << 64) % q
+        xs = [(1 << 85) - 1, 0, q, 6 * (q - 1) ** 2 + q - 1] + [RNG.getrandbits(85) for _ in range(300)]
+        for x in xs:
+            lo, hi = x & M64, x >> 64
+            f = (lo & ~(1 << 63)) + (c63 if lo >> 63 else 0) + hi * c64
+            assert f < 1 << 64 and f % q == x % q
+            a0, a1 = f & M32, f >> 32
+            qe = (a1 * mu + ((a0 * mu) >> 32)) >> 32
+            r = (f - qe * q) & M64
+            assert r < 3 * q and r % q == x % q
+            assert 64 * r * (q - 1) < 1 << 96
