@@ -839,7 +839,11 @@ def run_paper_shape(args, dist: Dist):
     torch.cuda.synchronize()
     evs[0].record(stream)
     for i in range(steps):
+        if i == 0:  # one LT's launches for profilers (ncu --nvtx --nvtx-include "timed_lt/")
+            torch.cuda.nvtx.range_push("timed_lt")
         g.lt_eval(ct, f, "th", split, out=out)
+        if i == 0:
+            torch.cuda.nvtx.range_pop()
         evs[i + 1].record(stream)
     torch.cuda.synchronize()
     dist.barrier()

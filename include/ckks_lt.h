@@ -281,9 +281,9 @@ ckks_status lt_autotune_batch(ckks_ctx* ctx, lt_algo algo, uint32_t count, const
 /* The tile lt_autotune measured for the shape (algo, f, level) besides its
  * split: outer rotation indices per CTA of the diagonal multiply-accumulate
  * kernel (Alg. 2 lines 8-14) and positions per CTA, each 0 for the default
- * (outer: the next power of two >= n'3, at most 8; positions: 256, two CTAs
- * per SM, or one with 8 outer indices).  lt_autotune times the default, half
- * the outer indices, and 512 positions (one CTA per SM) for its chosen split, and
+ * (outer: the next power of two >= n'3, at most 8; positions: 128, four
+ * CTAs per SM, or two with 8 outer indices).  lt_autotune times the default,
+ * half the outer indices, and 256 positions for its chosen split, and
  * lt_eval uses the fastest whenever it runs that split for that shape;
  * results do not depend on the tile.  Returns 1 and writes the tile, 0 if
  * the shape was not tuned, -1 on a null argument. */
@@ -398,7 +398,7 @@ ckks_status ckks_debug_diag_mac_waits(ckks_ctx* ctx, uint64_t wait_limit_ns, uin
 
 /* Test hook: every later LT on the context runs the diagonal kernel with this
  * tile (see lt_tuned_tile; outer_per_cta 0 or a power of two up to 8, at
- * most the default; positions_per_cta 0, 256 or 512), instead of the tuned or
+ * most the default; positions_per_cta 0, 128, 256 or 512), instead of the tuned or
  * default one; (0, 0) restores the normal choice.  Results do not depend on
  * the tile, which is what the test checks.  It changes the context like an
  * upload (no evaluation call may overlap it). */

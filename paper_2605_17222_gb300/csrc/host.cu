@@ -939,15 +939,15 @@ struct ModelEst {
 };
 // Rates of this library's kernels on GB300, fitted to LTs measured at N = 2^16,
 // level 24, D = 256 over the splits (1,64,4), (2,32,4), (4,16,4), (2,16,8),
-// (4,8,8) (time within 5% of each; DRAM bytes within 2% of ncu's per-LT sum
+// (1,32,8) (time within 3% of each; DRAM bytes within 2% of ncu's per-LT sum
 // for (1,64,4), (2,32,4) and (4,8,8)):
-//   effective HBM bandwidth of the streaming kernels                5.8e12 B/s
-//   K6 multiply-accumulates, 4 or fewer outer indices per CTA       8.85e11 /s
-//                            8 outer indices per CTA                6.6e11 /s
+//   effective HBM bandwidth of the streaming kernels                6.2e12 B/s
+//   K6 multiply-accumulates, 4 or fewer outer indices per CTA       9.5e11 /s
+//                            8 outer indices per CTA                7.0e11 /s
 //   NTT butterflies (about 1.35 us per 2^16-point limb transform)   3.9e11 /s
 //   DRAM traffic of a limb transform: 2.75 limbs (input, the two passes'
 //   intermediate mostly through DRAM, output)
-constexpr double M_BW = 5.8e12, M_MAC4 = 8.85e11, M_MAC8 = 6.6e11, M_NTT = 3.9e11, M_FIXED = 5e-5;
+constexpr double M_BW = 6.2e12, M_MAC4 = 9.5e11, M_MAC8 = 7.0e11, M_NTT = 3.9e11, M_FIXED = 5e-5;
 constexpr double M_NTT_LIMBS = 2.75;
 
 ModelEst model_th_est(const ckks_ctx* C, u32 level, u32 D, u32 n1, u32 n2, u32 n3) {
@@ -1095,10 +1095,10 @@ ckks_status ckks_debug_diag_mac_tile(ckks_ctx* ctx, uint32_t outer_per_cta, uint
         if (!ctx) fail(CKKS_EINVAL, "null argument");
         if (outer_per_cta & (outer_per_cta - 1) || outer_per_cta > (u32)DM_MAX_K3)
             fail(CKKS_EINVAL, "outer indices per CTA: 0 or a power of two up to 8");
-        if (positions_per_cta != 0 && positions_per_cta != 256 && positions_per_cta != 512)
-            fail(CKKS_EINVAL, "positions per CTA: 0, 256 or 512");
+        if (positions_per_cta != 0 && positions_per_cta != 128 && positions_per_cta != 256 && positions_per_cta != 512)
+            fail(CKKS_EINVAL, "positions per CTA: 0, 128, 256 or 512");
         ctx->dbg_tile_k3 = outer_per_cta;
-        ctx->dbg_tile_run = positions_per_cta == 256 ? 0 : positions_per_cta;
+        ctx->dbg_tile_run = positions_per_cta;
     });
 }
 
@@ -1552,14 +1552,14 @@ ckks_status lt_autotune(ckks_ctx* ctx, lt_algo algo, const ckks_ct* sample, cons
             ctx->tuned_tile[key] = {0u, 0u};
         }
         // the diagonal kernel's tile for the chosen split: fewer outer indices per CTA
-        // (half the default), and one CTA of 512 positions per SM instead of two of 256
+        // (half the default), and the other number of positions per CTA (see launch_ws)
         if (algo != LT_BSGS) {
             const lt_split t = th_form(ctx, level, f, algo, bsp);
             u32 k3 = 1;
             while (k3 < t.n3 && k3 < (u32)DM_MAX_K3) k3 *= 2;
             std::vector<std::pair<u32, u32>> tiles;
             if (k3 >= 2) tiles.push_back({k3 / 2, 0u});
-            if (k3 < (u32)DM_MAX_K3) tiles.push_back({0u, 512u});
+            tiles.push_back({0u, 256u});
             std::pair<u32, u32> btile{0u, 0u};
             for (const auto& tl : tiles) {
                 {

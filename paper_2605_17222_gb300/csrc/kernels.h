@@ -151,8 +151,7 @@ struct DiagMacArgs {
     u32 starve_step;
     // Tile (0 = default): outer indices per CTA (a power of two below the
     // default, which is the next power of two >= n3, at most 8) and positions
-    // per CTA (512 = one CTA per SM instead of two of 256).  Results do not
-    // depend on it.
+    // per CTA (128, 256 or 512; see launch_ws).  Results do not depend on it.
     u32 tile_k3, tile_run;
     // Batch of ciphertexts sharing the diagonals and keys: ciphertext b uses
     // c0[b], c1[b] as its lifted inputs and A[i] + b*bs_ab, B[i] + b*bs_ab,

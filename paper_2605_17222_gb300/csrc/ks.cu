@@ -943,20 +943,23 @@ static int k6_form() {
     return f;
 }
 
-// Tile of the warp-specialised K6: positions per CTA.  With four or fewer
-// outer indices per CTA, 256 positions and two CTAs per SM by default (3-5%
-// faster than one CTA of 512 at the N = 2^16 splits measured: two independent
-// stage rings per SM), 512 positions on request (tile_run = 512); with eight
-// outer accumulators per thread, 256 positions and one CTA per SM (register
-// budget).
+// Tile of the warp-specialised K6: positions per CTA.  More CTAs per SM give
+// more independent stage rings, which is what the compute warps wait on:
+// with four or fewer outer indices per CTA the default is 128 positions and
+// four CTAs per SM (measured against two of 256 and one of 512 at the N = 2^16
+// splits: 4% and 9% faster), tile_run = 256 or 512 on request; with eight
+// outer accumulators per thread (register budget) 128 positions and two CTAs
+// per SM by default (2% faster than one of 256), 256 on request.
 template <int K3>
 bool launch_ws(const DiagMacArgs& a, cudaStream_t st) {
     const bool mid = a.n2 > 1;
     if constexpr (K3 >= 8) {
-        return mid ? try_ws<K3, 256, 2, 6>(a, st) : try_ws<K3, 256, 4, 0>(a, st);
+        if (a.tile_run == 256) return mid ? try_ws<K3, 256, 2, 6>(a, st) : try_ws<K3, 256, 4, 0>(a, st);
+        return mid ? try_ws<K3, 128, 2, 6, 2>(a, st) : try_ws<K3, 128, 4, 0, 2>(a, st);
     } else {
         if (a.tile_run == 512) return mid ? try_ws<K3, 512, 2, 6>(a, st) : try_ws<K3, 512, 4, 0>(a, st);
-        return mid ? try_ws<K3, 256, 2, 6, 2>(a, st) : try_ws<K3, 256, 4, 0, 2>(a, st);
+        if (a.tile_run == 256) return mid ? try_ws<K3, 256, 2, 6, 2>(a, st) : try_ws<K3, 256, 4, 0, 2>(a, st);
+        return mid ? try_ws<K3, 128, 2, 6, 4>(a, st) : try_ws<K3, 128, 4, 0, 4>(a, st);
     }
 }
 

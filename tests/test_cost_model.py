@@ -14,7 +14,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-BW, MAC4, MAC8, NTT, FIXED, NTT_LIMBS = 5.8e12, 8.85e11, 6.6e11, 3.9e11, 5e-5, 2.75
+BW, MAC4, MAC8, NTT, FIXED, NTT_LIMBS = 6.2e12, 9.5e11, 7.0e11, 3.9e11, 5e-5, 2.75
 
 
 def model(level, D, n1, n2, n3, log_n=16, K=4, alpha=4):
@@ -54,10 +54,10 @@ def test_dram_bytes_within_two_percent(measured):
         assert abs(b - m["total"]) / m["total"] < 0.02, (key, b, m["total"])
 
 
-def test_lt_time_within_five_percent_and_ranking(measured):
+def test_lt_time_within_three_percent_and_ranking(measured):
     for key, ms in measured["lt_ms"].items():
         _, s = model(24, 256, *split_of(key))
-        assert abs(s * 1e3 - ms) / ms < 0.05, (key, s * 1e3, ms)
+        assert abs(s * 1e3 - ms) / ms < 0.03, (key, s * 1e3, ms)
     # the model orders the measured splits as the measurements do, fastest first
     by_meas = sorted(measured["lt_ms"], key=measured["lt_ms"].get)
     by_model = sorted(measured["lt_ms"], key=lambda k: model(24, 256, *split_of(k))[1])

@@ -163,7 +163,7 @@ def test_toy_dh_autotuner_times_both_schedules(toy):
 @pytest.mark.parametrize("split", [(4, 4, 4), (2, 4, 8), (1, 8, 8)])
 def test_toy_every_diagonal_kernel_tile(toy, split):
     """Every tile of the diagonal kernel (outer indices per CTA below the
-    default, 512 positions with one CTA per SM) gives the oracle's residues."""
+    default; 128, 256 or 512 positions per CTA) gives the oracle's residues."""
     pb, g, f = toy
     ct = g.ct_from_host(np.stack(pb.ct))
     want = oracle_lt(pb, "th", split)
@@ -172,7 +172,7 @@ def test_toy_every_diagonal_kernel_tile(toy, split):
         k3 *= 2
     try:
         for outer in sorted({0, k3 // 2 or 0, 1}):
-            for pos in (0, 512):
+            for pos in (0, 128, 256, 512):
                 g.debug_diag_mac_tile(outer, pos)
                 out, _ = g.lt_eval(ct, f, "th", split)
                 assert_same(out.numpy(), want, f"toy {split} tile ({outer}, {pos})")
