@@ -373,11 +373,14 @@ void op_decompose_batch(ckks_ctx* C, u32 level, const std::vector<const u64*>& c
         u64* Yp = Y + (size_t)p * level * N;
         for (u32 b = 0; b < beta; b++) {
             const u32 first = b * C->alpha, n = std::min(C->alpha, level - first);
+            // the digit's words are canonical residues of its moduli: below 2^41 if every one is
+            bool small = true;
+            for (u32 j = first; j < first + n; j++) small = small && C->mods[j] < (1ull << 41);
             for (u32 t = 0; t < ext; t++) {
                 if (t >= first && t < first + n) continue;
                 fj.push_back(FwdJob{Yp + (size_t)first * N, digits[p] + ((size_t)b * ext + t) * N,
                                     LC.dec_tab + ((size_t)b * ext + t) * C->alpha, nullptr, nullptr, 0, 0,
-                                    C->gmod(level, t), n});
+                                    C->gmod(level, t), n | (small ? 1u << 16 : 0u)});
             }
         }
     }

@@ -19,6 +19,8 @@ struct NttTables {
 // One limb of a forward NTT.
 //   pass 1 load : nsrc == 0 -> src[x];
 //                 nsrc  > 0 -> sum_j src[j*N + x] * bcst[j] mod q   (basis conversion, Eq. 3)
+//                 (bits 0-15: the source count; bit 16: every source word is
+//                 below 2^41, which with a target 2^32 < q < 2^41 allows 96-bit sums)
 //   pass 2 store: subout == nullptr -> dst[x] = X;
 //                 otherwise subout[x] = (subx[x] - X) * c mod q        (ModDown tail, Eq. 4)
 // Pass 1 writes dst; pass 2 runs in place on dst.

@@ -282,6 +282,49 @@ __device__ __forceinline__ void fwd_cols_stages(u64 (&x)[16], u64* sm, u32 u, u3
     }
 }
 
+// Basis conversion (Eq. 3) of a column-pass thread's 16 words, NS source
+// limbs known at compile time (the constants held in registers), staged
+// through the thread's own slots of the exchange buffer.  SMALL: sources and
+// target below 2^41 (and the target above 2^32), so the four-term sums stay
+// in 96 bits (mac96) and are reduced to [0, 3q) by a fold below 2^64 and a
+// 32-bit quotient estimate (mu = floor(2^64 / q)); otherwise 128-bit sums
+// reduced lazily to [0, 4q).  Either range feeds the butterflies.
+template <int LOGS, int NS, bool SMALL>
+__device__ __forceinline__ void bconv_words(u64* sm, const FwdJob& J, u32 u, u32 c, u32 col, u32 N, u32 C,
+                                            const ModC& m) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
+    u64 cst[NS];
+#pragma unroll
+    for (int j = 0; j < NS; j++) cst[j] = J.bcst[j];
+    const u64 q = m.q;
+    const u64 c64 = 0 - q * m.mu_hi;                     // 2^64 mod q (mu_hi = floor(2^64 / q))
+    const u64 c63 = (c64 + ((c64 & 1) ? q : 0)) >> 1;   // 2^63 mod q
+    const u32 mu32 = (u32)m.mu_hi;
+    const u64* src = J.src + (size_t)u * C + col;
+#pragma unroll 4
+    for (int v = 0; v < 16; v++) {
+        const u64* p = src + (size_t)(TPL * v) * C;
+        u64 y[NS];
+#pragma unroll
+        for (int j = 0; j < NS; j++) y[j] = p[(size_t)j * N];
+        u64 r;
+        if constexpr (SMALL) {
+            U96 acc{0, 0};
+#pragma unroll
+            for (int j = 0; j < NS; j++) mac96(acc, y[j], cst[j]);
+            const u64 f = (acc.lo & ~(1ull << 63)) + ((acc.lo >> 63) ? c63 : 0) + (u64)acc.hi * c64;
+            const u64 qe = ((u64)(u32)(f >> 32) * mu32 + __umulhi((u32)f, mu32)) >> 32;
+            r = f - qe * q;
+        } else {
+            U128 acc{0, 0};
+#pragma unroll
+            for (int j = 0; j < NS; j++) mac128(acc, y[j], cst[j]);
+            r = reduce128_lazy(acc, m);
+        }
+        sm[(u + TPL * v) * W + c] = r;
+    }
+}
+
 template <int LOGS, bool BCONV>
 __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<FwdJob> jobs) {
@@ -298,14 +341,20 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
     if constexpr (BCONV) {
         // basis conversion (Eq. 3) of the thread's 16 words, staged through its
         // own slots of the exchange buffer so that this part stays a compact loop
-        const u64* bc = J.bcst;
-        const u32 ns = J.nsrc;
+        const u32 ns = J.nsrc & 0xFFFFu;
+        const bool small = (J.nsrc >> 16) && q > (1ull << 32) && q < (1ull << 41);
+        if (ns == 4 && small) bconv_words<LOGS, 4, true>(sm, J, u, c, col, N, C, m);
+        else if (ns == 4) bconv_words<LOGS, 4, false>(sm, J, u, c, col, N, C, m);
+        else if (ns == 5) bconv_words<LOGS, 5, false>(sm, J, u, c, col, N, C, m);
+        else {
+            const u64* bc = J.bcst;
 #pragma unroll 4
-        for (int v = 0; v < 16; v++) {
-            const u64* src = J.src + (size_t)(u + TPL * v) * C + col;
-            U128 acc{0, 0};
-            for (u32 j = 0; j < ns; j++) mac128(acc, src[(size_t)j * N], bc[j]);
-            sm[(u + TPL * v) * W + c] = reduce128_lazy(acc, m);  // [0, 4q): both butterfly forms take it
+            for (int v = 0; v < 16; v++) {
+                const u64* src = J.src + (size_t)(u + TPL * v) * C + col;
+                U128 acc{0, 0};
+                for (u32 j = 0; j < ns; j++) mac128(acc, src[(size_t)j * N], bc[j]);
+                sm[(u + TPL * v) * W + c] = reduce128_lazy(acc, m);  // [0, 4q): both butterfly forms take it
+            }
         }
 #pragma unroll
         for (int v = 0; v < 16; v++) x[v] = sm[(u + TPL * v) * W + c];
@@ -551,7 +600,7 @@ void fwd_impl(const NttTables& T, const Jobs<FwdJob>& p, int n, bool bconv, bool
     const double half = (double)n * (N / 2);  // butterflies per stage over the launch's limbs
     double bconv_macs = 0;
     if (bconv)
-        for (int i = 0; i < n; i++) bconv_macs += (double)p.j[i].nsrc * N;
+        for (int i = 0; i < n; i++) bconv_macs += (double)(p.j[i].nsrc & 0xFFFFu) * N;
     {
         ProfScope ps(K_FWD_COLS, st, bconv_macs, half * LR);
         if (bconv) k_fwd_cols<LR, true><<<g1, THREADS, 0, st>>>(T, p);
@@ -646,7 +695,7 @@ __global__ void __launch_bounds__(PROBE_THREADS, 4) k_probe_bfly(const ulonglong
 
 void launch_fwd_ntt(const NttTables& T, const FwdJob* jobs, int njobs, cudaStream_t st) {
     if (njobs <= 0) return;
-    const bool bconv = jobs[0].nsrc > 0, submul = jobs[0].subout != nullptr;
+    const bool bconv = (jobs[0].nsrc & 0xFFFFu) > 0, submul = jobs[0].subout != nullptr;
     for_chunks(jobs, njobs, [&](const Jobs<FwdJob>& p, int n) {
         NTT_DISPATCH(fwd_impl, bconv, submul);
         count_launch(2);

@@ -175,3 +175,31 @@ def test_middle_sum_reduction_for_the_96_bit_products():
             r = (f - qe * q) & M64
             assert r < 3 * q and r % q == x % q
             assert 64 * r * (q - 1) < 1 << 96
+
+
+def test_column_pass_basis_conversion_96_bit_path():
+    """The NTT column pass's 96-bit basis conversion: 2^64 mod q and 2^63 mod q
+    derived from mu_hi = floor(2^128 / q) >> 64 as the kernel derives them,
+    four products of words below 2^41 summed by mac96, then the fold and the
+    32-bit quotient estimate: a word in [0, 3q) congruent to the sum (below
+    4q, the butterflies' input range)."""
+    for q in small_moduli():
+        mu_hi = ((1 << 128) // q) >> 64
+        c64 = (0 - q * mu_hi) & M64
+        c63 = (c64 + (q if c64 & 1 else 0)) >> 1
+        assert c64 == (1 << 64) % q and c63 == (1 << 63) % q
+        mu32 = mu_hi & M32
+        assert mu32 == mu_hi
+        for trial in range(200):
+            ys = [RNG.randrange(1 << 41) if trial % 3 else (1 << 41) - 1 for _ in range(4)]
+            cs = [RNG.randrange(q) if trial % 5 else q - 1 for _ in range(4)]
+            lo = hi = 0
+            for y, cst in zip(ys, cs):
+                lo, hi = mac96(lo, hi, y, cst)
+            x = sum(y * cst for y, cst in zip(ys, cs))
+            assert lo | (hi << 64) == x
+            f = (lo & ~(1 << 63)) + (c63 if lo >> 63 else 0) + hi * c64
+            assert f < 1 << 64
+            qe = ((f >> 32) * mu32 + (((f & M32) * mu32) >> 32)) >> 32
+            r = (f - qe * q) & M64
+            assert r < 3 * q and r % q == x % q
