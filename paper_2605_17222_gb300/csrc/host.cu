@@ -385,13 +385,16 @@ void op_decompose_batch(ckks_ctx* C, u32 level, const std::vector<const u64*>& c
         }
     }
     launch_fwd_ntt(C->T, fj.data(), (int)fj.size(), st);
+    // each digit's own limbs are the (gathered) input limbs: one copy launch for all of them
+    std::vector<AddJob> cj;
+    cj.reserve((size_t)cnt * level);
     for (u32 p = 0; p < cnt; p++)
         for (u32 b = 0; b < beta; b++) {
             const u32 first = b * C->alpha, n = std::min(C->alpha, level - first);
-            u64* dst = digits[p] + ((size_t)b * ext + first) * N;
-            if (gal) launch_automorphism(cs[p] + (size_t)first * N, dst, n, gal, C->log_n, st);
-            else CK(cudaMemcpyAsync(dst, cs[p] + (size_t)first * N, (size_t)n * N * 8, cudaMemcpyDeviceToDevice, st));
+            for (u32 j = first; j < first + n; j++)
+                cj.push_back(AddJob{cs[p] + (size_t)j * N, nullptr, digits[p] + ((size_t)b * ext + j) * N, j, 0});
         }
+    launch_add_gather((const ModC*)C->d_mods.p, cj.data(), (int)cj.size(), gal, 0, C->log_n, st);
 }
 
 void op_decompose(ckks_ctx* C, u32 level, const u64* c, u32 gal, u64* digits, u64* Y, cudaStream_t st) {
