@@ -190,6 +190,18 @@ __device__ __forceinline__ u64 canon4(u64 x, u64 q) {
 // Any 64-bit word -> [0, 2q): the Shoup product by 1 (floor(2^64 / q) = mu_hi).
 __device__ __forceinline__ u64 red2(u64 x, u64 q, u64 mu_hi) { return x - __umul64hi(x, mu_hi) * q; }
 
+// x < 2^50 -> [0, 3q) for 2^32 < q < 2^41, with mu32 = floor(2^64 / q) (below
+// 2^32).  The estimate qe = floor(floor(x / 2^32) mu32 / 2^32) never exceeds
+// floor(x / q) and falls short of it by at most 2: the dropped low word of x
+// is worth below 2^32 / q < 1, mu32's truncation below floor(x / 2^32) / 2^32
+// < 2^-14, and the floor below 1.  One 32 x 32 product and one small product
+// by q, instead of the 64 x 64 high product of red2.
+__device__ __forceinline__ u64 red3_small(u64 x, u64 q, u32 mu32) {
+    const u64 qe = ((u64)(u32)(x >> 32) * mu32) >> 32;
+    return x - qe * q;
+}
+__device__ __forceinline__ bool small_q(u64 q) { return q > (1ull << 32) && q < (1ull << 41); }
+
 // ------------------------------------------------------------------ growing butterflies
 // For moduli well below 2^64 the per-butterfly conditional subtraction that
 // keeps a lazy word bounded can be dropped inside a pass:
@@ -230,13 +242,16 @@ __device__ __forceinline__ void ct(u64& a, u64& b, const ulonglong2* tab, u32 id
     }
 }
 
-template <bool GROW>
+// GM = 0: reducing (gs_bfly); 1: growing, exact lazy Shoup product in [0, 2q);
+// 2: growing, approximate quotient (mul_shoup_approx) in [0, 4q) -- the
+// caller's M then doubles from 4q on (see the inverse passes).
+template <int GM>
 __device__ __forceinline__ void gs(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q, u64 M) {
-    if constexpr (GROW) {
+    if constexpr (GM > 0) {
         u64 w, ws;
         tw_at(tab, idx, w, ws);
         const u64 s = a + b;
-        b = mul_shoup_lazy(a - b + M, w, ws, q);
+        b = GM == 2 ? mul_shoup_approx(a - b + M, w, ws, q) : mul_shoup_lazy(a - b + M, w, ws, q);
         a = s;
     } else {
         gs_bfly(a, b, tab, idx, q);
@@ -325,12 +340,12 @@ __device__ __forceinline__ void bconv_words(u64* sm, const FwdJob& J, u32 u, u32
     }
 }
 
-template <int LOGS, bool BCONV>
+template <int LOGN, int LOGS, bool BCONV>
 __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<FwdJob> jobs) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
     __shared__ u64 sm[S * W];
-    const u32 log_n = T.log_n, N = 1u << log_n, C = N >> LOGS;
+    constexpr u32 N = 1u << LOGN, C = N >> LOGS;
     const u32 c = threadIdx.x % W, u = threadIdx.x / W;
     const u32 col = blockIdx.x * W + c;
     const FwdJob& J = jobs.j[blockIdx.y];
@@ -399,26 +414,21 @@ __device__ __forceinline__ void fwd_rows_stages(u64 (&x)[16], u64* sr, u32 u, u3
     }
 }
 
-template <int LOGS, bool SUBMUL>
-__global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__ NttTables T,
-                                                      const __grid_constant__ Jobs<FwdJob> jobs) {
-    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
-    __shared__ u64 sm[B * SP];
-    const u32 log_n = T.log_n, N = 1u << log_n, log_r = log_n - LOGS;
-    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
-    const u32 row = blockIdx.x * B + rl;
-    const FwdJob& J = jobs.j[blockIdx.y];
-    const ModC m = T.mods[J.mod];
+// The row pass of one limb in one arithmetic class (chosen once per block, so
+// that each class is compiled and register-allocated on its own):
+// AR = 0: reducing butterflies, words below 4q;
+// AR = 1: growing butterflies, words below 68q, reduced by red2;
+// AR = 2: growing butterflies with 2^32 < q < 2^41, reduced by red3_small.
+template <int LOGN, int LOGS, bool SUBMUL, int AR>
+__device__ __forceinline__ void fwd_rows_limb(const FwdJob& J, const ModC& m, const ulonglong2* tw, u64* sr,
+                                              u32 u, u32 row) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, log_r = LOGN - LOGS;
     const u64 q = m.q;
-    const ulonglong2* tw = T.psi + (size_t)J.mod * N;
     const size_t base = (size_t)row * S;
-    u64* sr = sm + rl * SP;
     u64 x[16];
 #pragma unroll
     for (int v = 0; v < 16; v++) x[v] = J.dst[base + u + TPL * v];
-    const bool grow = q < FWD_GROW_MAX;
-    if (grow) fwd_rows_stages<LOGS, true>(x, sr, u, row, log_r, tw, q);
-    else fwd_rows_stages<LOGS, false>(x, sr, u, row, log_r, tw, q);
+    fwd_rows_stages<LOGS, (AR > 0)>(x, sr, u, row, log_r, tw, q);
     __syncwarp();
 #pragma unroll
     for (int v = 0; v < 16; v++) sr[pad16(16 * u + v)] = x[v];
@@ -428,7 +438,11 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__
         const u32 xi = u + TPL * v;
         const u64 y = sr[pad16(xi)];
         u64 val;
-        if (grow) {  // below 68q
+        if constexpr (AR == 2) {  // below 68q < 2^48 -> [0, 3q)
+            val = red3_small(y, q, (u32)m.mu_hi);
+            val = val >= 2 * q ? val - 2 * q : val;
+            val = val >= q ? val - q : val;
+        } else if constexpr (AR == 1) {  // below 68q
             val = red2(y, q, m.mu_hi);
             val = val >= q ? val - q : val;
         } else {  // below 4q
@@ -442,10 +456,34 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__
     }
 }
 
+template <int LOGN, int LOGS, bool SUBMUL>
+__global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__ NttTables T,
+                                                      const __grid_constant__ Jobs<FwdJob> jobs) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
+    __shared__ u64 sm[B * SP];
+    constexpr u32 N = 1u << LOGN;
+    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
+    const u32 row = blockIdx.x * B + rl;
+    const FwdJob& J = jobs.j[blockIdx.y];
+    const ModC m = T.mods[J.mod];
+    const ulonglong2* tw = T.psi + (size_t)J.mod * N;
+    u64* sr = sm + rl * SP;
+    if (small_q(m.q)) fwd_rows_limb<LOGN, LOGS, SUBMUL, 2>(J, m, tw, sr, u, row);
+    else if (m.q < FWD_GROW_MAX) fwd_rows_limb<LOGN, LOGS, SUBMUL, 1>(J, m, tw, sr, u, row);
+    else fwd_rows_limb<LOGN, LOGS, SUBMUL, 0>(J, m, tw, sr, u, row);
+}
+
 // ------------------------------------------------------------------ inverse, row pass
 // GS stages with half-width t = 1..S/2 (m = N/2t, twiddle psi^-brv(m + row S/2t + x/2t)).
-// Growing form: words enter below q; the i-th stage of the pass takes M = q 2^i.
-template <int LOGS, bool GROW>
+// Growing forms: words enter below q.  GM = 1: the i-th stage of the pass takes
+// M = q 2^i (outputs below 2^LOGS q).  GM = 2 (products in [0, 4q)): stage 0
+// takes M = q and leaves words below 4q, stage i > 0 takes M = q 2^(i+1)
+// (outputs below 2^(LOGS+1) q).
+template <int GM>
+__device__ __forceinline__ u64 inv_rows_m(u64 q, int lt) {
+    return GM == 2 ? (lt == 0 ? q : q << (lt + 1)) : q << lt;
+}
+template <int LOGS, int GM>
 __device__ __forceinline__ void inv_rows_stages(u64 (&x)[16], u64* sr, u32 u, u32 row, u32 N,
                                                 const ulonglong2* tw, u64 q) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16;
@@ -453,10 +491,10 @@ __device__ __forceinline__ void inv_rows_stages(u64 (&x)[16], u64* sr, u32 u, u3
     for (int lt = 0; lt < LOGS - 4; lt++) {  // t = 1 .. TPL/2
         const int t = 1 << lt;
         const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
-        const u64 M = q << lt;
+        const u64 M = inv_rows_m<GM>(q, lt);
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & t)) gs<GROW>(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (lt + 1)), q, M);
+            if (!(v & t)) gs<GM>(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (lt + 1)), q, M);
     }
     __syncwarp();
 #pragma unroll
@@ -468,32 +506,25 @@ __device__ __forceinline__ void inv_rows_stages(u64 (&x)[16], u64* sr, u32 u, u3
     for (int k = 0; k < 4; k++) {  // t = TPL * 2^k
         const int lt = (LOGS - 4) + k;
         const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
-        const u64 M = q << lt;
+        const u64 M = inv_rows_m<GM>(q, lt);
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & (1 << k))) gs<GROW>(x[v], x[v + (1 << k)], tw, b0 + (v >> (k + 1)), q, M);
+            if (!(v & (1 << k))) gs<GM>(x[v], x[v + (1 << k)], tw, b0 + (v >> (k + 1)), q, M);
     }
 }
 
-template <int LOGS, bool GATHER>
-__global__ void __launch_bounds__(THREADS, 4) k_inv_rows(const __grid_constant__ NttTables T,
-                                                      const __grid_constant__ Jobs<InvJob> jobs) {
-    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
-    __shared__ u64 sm[B * SP];
-    const u32 log_n = T.log_n, N = 1u << log_n;
-    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
-    const u32 row = blockIdx.x * B + rl;
-    const InvJob& J = jobs.j[blockIdx.y];
-    const ModC m = T.mods[J.mod];
+// The inverse row pass of one limb in one arithmetic class GM (gs above).
+template <int LOGN, int LOGS, bool GATHER, int GM>
+__device__ __forceinline__ void inv_rows_limb(const InvJob& J, const ModC& m, const ulonglong2* tw, u64* sr,
+                                              u32 u, u32 row) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, N = 1u << LOGN;
     const u64 q = m.q;
-    const ulonglong2* tw = T.ipsi + (size_t)J.mod * N;
     const size_t base = (size_t)row * S;
-    u64* sr = sm + rl * SP;
     u64 x[16];
 #pragma unroll
     for (int v = 0; v < 16; v++) {
         const u32 xi = u + TPL * v;
-        if constexpr (GATHER) x[v] = J.src[auto_src((u32)(base + xi), J.gal, log_n)];
+        if constexpr (GATHER) x[v] = J.src[auto_src((u32)(base + xi), J.gal, LOGN)];
         else x[v] = J.src[base + xi];
     }
 #pragma unroll
@@ -501,22 +532,44 @@ __global__ void __launch_bounds__(THREADS, 4) k_inv_rows(const __grid_constant__
     __syncwarp();
 #pragma unroll
     for (int v = 0; v < 16; v++) x[v] = sr[pad16(16 * u + v)];
-    if (q < INV_GROW_MAX) {
-        inv_rows_stages<LOGS, true>(x, sr, u, row, N, tw, q);
+    inv_rows_stages<LOGS, GM>(x, sr, u, row, N, tw, q);
+    if constexpr (GM == 2) {
+#pragma unroll
+        for (int v = 0; v < 16; v++) {  // below 2^(LOGS+1) q <= 2^50 -> [0, 3q) -> [0, 2q)
+            const u64 r = red3_small(x[v], q, (u32)m.mu_hi);
+            x[v] = r >= 2 * q ? r - 2 * q : r;
+        }
+    } else if constexpr (GM == 1) {
 #pragma unroll
         for (int v = 0; v < 16; v++) x[v] = red2(x[v], q, m.mu_hi);  // below 2^8 q -> [0, 2q)
-    } else {
-        inv_rows_stages<LOGS, false>(x, sr, u, row, N, tw, q);  // stays in [0, 2q)
-    }
+    }  // GM == 0 stays in [0, 2q)
 #pragma unroll
     for (int v = 0; v < 16; v++) J.tmp[base + u + TPL * v] = x[v];
+}
+
+template <int LOGN, int LOGS, bool GATHER>
+__global__ void __launch_bounds__(THREADS, 3) k_inv_rows(const __grid_constant__ NttTables T,
+                                                      const __grid_constant__ Jobs<InvJob> jobs) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
+    __shared__ u64 sm[B * SP];
+    constexpr u32 N = 1u << LOGN;
+    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
+    const u32 row = blockIdx.x * B + rl;
+    const InvJob& J = jobs.j[blockIdx.y];
+    const ModC m = T.mods[J.mod];
+    const ulonglong2* tw = T.ipsi + (size_t)J.mod * N;
+    u64* sr = sm + rl * SP;
+    if (small_q(m.q)) inv_rows_limb<LOGN, LOGS, GATHER, 2>(J, m, tw, sr, u, row);
+    else if (m.q < INV_GROW_MAX) inv_rows_limb<LOGN, LOGS, GATHER, 1>(J, m, tw, sr, u, row);
+    else inv_rows_limb<LOGN, LOGS, GATHER, 0>(J, m, tw, sr, u, row);
 }
 
 // ------------------------------------------------------------------ inverse, column pass
 // GS stages with half-width C*t_r, t_r = 1..S/2 (m = S/2t_r, twiddle psi^-brv(m + r/2t_r)),
 // then the scaling by c (N^-1 and any per-limb constant).
-// Growing form: words enter below 2q; the i-th stage of the pass takes M = 2q 2^i.
-template <int LOGS, bool GROW>
+// Growing forms: words enter below 2q; the i-th stage of the pass takes M = 2q 2^i,
+// which also bounds the [0, 4q) products of GM = 2 (outputs below 2^(LOGS+1) q).
+template <int LOGS, int GM>
 __device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u32 c, const ulonglong2* tw, u64 q) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
 #pragma unroll
@@ -525,7 +578,7 @@ __device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u3
         const u64 M = (2 * q) << lt;
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & t)) gs<GROW>(x[v], x[v + t], tw, (S >> (lt + 1)) + ((16 * u + v) >> (lt + 1)), q, M);
+            if (!(v & t)) gs<GM>(x[v], x[v + t], tw, (S >> (lt + 1)) + ((16 * u + v) >> (lt + 1)), q, M);
     }
 #pragma unroll
     for (int v = 0; v < 16; v++) sm[(16 * u + v) * W + c] = x[v];
@@ -538,29 +591,44 @@ __device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u3
         const u64 M = (2 * q) << lt;
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & (1 << k))) gs<GROW>(x[v], x[v + (1 << k)], tw, (S >> (lt + 1)) + (v >> (k + 1)), q, M);
+            if (!(v & (1 << k))) gs<GM>(x[v], x[v + (1 << k)], tw, (S >> (lt + 1)) + (v >> (k + 1)), q, M);
     }
 }
 
-template <int LOGS>
-__global__ void __launch_bounds__(THREADS, 4) k_inv_cols(const __grid_constant__ NttTables T,
+// The inverse column pass of one limb in one arithmetic class GM, then the
+// scaling by c: mul_shoup reduces any 64-bit word fully; the approximate
+// product (GM = 2) takes it to [0, 4q) first.
+template <int LOGN, int LOGS, int GM>
+__device__ __forceinline__ void inv_cols_limb(const InvJob& J, u64 q, const ulonglong2* tw, u64* sm, u32 u, u32 c,
+                                              u32 col) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, C = (1u << LOGN) >> LOGS;
+    u64 x[16];
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = J.tmp[(size_t)(16 * u + v) * C + col];
+    inv_cols_stages<LOGS, GM>(x, sm, u, c, tw, q);
+#pragma unroll
+    for (int v = 0; v < 16; v++) {
+        u64 y;
+        if constexpr (GM == 2) y = canon4(mul_shoup_approx(x[v], J.c, J.c_sh, q), q);
+        else y = mul_shoup(x[v], J.c, J.c_sh, q);
+        J.dst[(size_t)(u + TPL * v) * C + col] = y;
+    }
+}
+
+template <int LOGN, int LOGS>
+__global__ void __launch_bounds__(THREADS, 3) k_inv_cols(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<InvJob> jobs) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
     __shared__ u64 sm[S * W];
-    const u32 log_n = T.log_n, N = 1u << log_n, C = N >> LOGS;
+    constexpr u32 N = 1u << LOGN;
     const u32 c = threadIdx.x % W, u = threadIdx.x / W;
     const u32 col = blockIdx.x * W + c;
     const InvJob& J = jobs.j[blockIdx.y];
     const u64 q = T.mods[J.mod].q;
     const ulonglong2* tw = T.ipsi + (size_t)J.mod * N;
-    u64 x[16];
-#pragma unroll
-    for (int v = 0; v < 16; v++) x[v] = J.tmp[(size_t)(16 * u + v) * C + col];
-    if (q < INV_GROW_MAX) inv_cols_stages<LOGS, true>(x, sm, u, c, tw, q);
-    else inv_cols_stages<LOGS, false>(x, sm, u, c, tw, q);
-    // mul_shoup reduces any 64-bit word fully
-#pragma unroll
-    for (int v = 0; v < 16; v++) J.dst[(size_t)(u + TPL * v) * C + col] = mul_shoup(x[v], J.c, J.c_sh, q);
+    if (small_q(q)) inv_cols_limb<LOGN, LOGS, 2>(J, q, tw, sm, u, c, col);
+    else if (q < INV_GROW_MAX) inv_cols_limb<LOGN, LOGS, 1>(J, q, tw, sm, u, c, col);
+    else inv_cols_limb<LOGN, LOGS, 0>(J, q, tw, sm, u, c, col);
 }
 
 __global__ void k_automorphism(const u64* __restrict__ in, u64* __restrict__ out, u32 gal, u32 log_n) {
@@ -603,13 +671,13 @@ void fwd_impl(const NttTables& T, const Jobs<FwdJob>& p, int n, bool bconv, bool
         for (int i = 0; i < n; i++) bconv_macs += (double)(p.j[i].nsrc & 0xFFFFu) * N;
     {
         ProfScope ps(K_FWD_COLS, st, bconv_macs, half * LR);
-        if (bconv) k_fwd_cols<LR, true><<<g1, THREADS, 0, st>>>(T, p);
-        else k_fwd_cols<LR, false><<<g1, THREADS, 0, st>>>(T, p);
+        if (bconv) k_fwd_cols<LR + LC, LR, true><<<g1, THREADS, 0, st>>>(T, p);
+        else k_fwd_cols<LR + LC, LR, false><<<g1, THREADS, 0, st>>>(T, p);
     }
     {
         ProfScope ps(K_FWD_ROWS, st, 0, half * LC);
-        if (submul) k_fwd_rows<LC, true><<<g2, THREADS, 0, st>>>(T, p);
-        else k_fwd_rows<LC, false><<<g2, THREADS, 0, st>>>(T, p);
+        if (submul) k_fwd_rows<LR + LC, LC, true><<<g2, THREADS, 0, st>>>(T, p);
+        else k_fwd_rows<LR + LC, LC, false><<<g2, THREADS, 0, st>>>(T, p);
     }
 }
 
@@ -620,12 +688,12 @@ void inv_impl(const NttTables& T, const Jobs<InvJob>& p, int n, bool gather, cud
     const double half = (double)n * (N / 2);
     {
         ProfScope ps(K_INV_ROWS, st, 0, half * LC);
-        if (gather) k_inv_rows<LC, true><<<g2, THREADS, 0, st>>>(T, p);
-        else k_inv_rows<LC, false><<<g2, THREADS, 0, st>>>(T, p);
+        if (gather) k_inv_rows<LR + LC, LC, true><<<g2, THREADS, 0, st>>>(T, p);
+        else k_inv_rows<LR + LC, LC, false><<<g2, THREADS, 0, st>>>(T, p);
     }
     {
         ProfScope ps(K_INV_COLS, st, 0, half * LR);
-        k_inv_cols<LR><<<g1, THREADS, 0, st>>>(T, p);
+        k_inv_cols<LR + LC, LR><<<g1, THREADS, 0, st>>>(T, p);
     }
 }
 
@@ -636,7 +704,7 @@ void inv_impl(const NttTables& T, const Jobs<InvJob>& p, int n, bool gather, cud
         case 13: IMPL<7, 6>(T, p, n, __VA_ARGS__, st); break;    \
         case 14: IMPL<7, 7>(T, p, n, __VA_ARGS__, st); break;    \
         case 15: IMPL<8, 7>(T, p, n, __VA_ARGS__, st); break;    \
-        default: IMPL<8, 8>(T, p, n, __VA_ARGS__, st); break;    \
+        default: IMPL<8, 8>(T, p, n, __VA_ARGS__, st); break; /* 16: contexts take 12..16 */ \
     }
 
 // ------------------------------------------------------------------ integer-rate probes

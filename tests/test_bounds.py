@@ -10,7 +10,10 @@ its comment claims, so that a change to either side has something to fail.
   * K6's fold of a middle-layer sum x = sum_b d_b k_b + A (beta <= 8, q < 2^41)
     is below 2^64, congruent to x mod q, and 64 of its products with a word
     below q fit the 128-bit accumulators;
-  * the lazy 128-bit Barrett reduction's estimate leaves a remainder in [0, 4q).
+  * the lazy 128-bit Barrett reduction's estimate leaves a remainder in [0, 4q);
+  * for 2^32 < q < 2^41: the NTT epilogues' 32-bit quotient estimate leaves
+    [0, 3q) for words below 2^50, and the inverse passes' M schedule with
+    [0, 4q) products keeps every GS difference non-negative.
 """
 import random
 
@@ -203,3 +206,55 @@ def test_column_pass_basis_conversion_96_bit_path():
             qe = ((f >> 32) * mu32 + (((f & M32) * mu32) >> 32)) >> 32
             r = (f - qe * q) & M64
             assert r < 3 * q and r % q == x % q
+
+
+def red3_small(x, q):
+    """The NTT epilogues' reduction for 2^32 < q < 2^41: quotient estimate
+    floor(floor(x / 2^32) mu32 / 2^32), mu32 = floor(2^64 / q)."""
+    mu32 = (((1 << 128) // q) >> 64) & M32
+    assert mu32 == (1 << 64) // q
+    qe = ((x >> 32) * mu32) >> 32
+    return qe, (x - qe * q) & M64
+
+
+def test_small_modulus_epilogue_reduction():
+    """Words below 2^50 (68q after a forward transform, 2^9 q after an inverse
+    pass with [0, 4q) products) reduce to [0, 3q): the estimate never exceeds
+    floor(x / q) and falls short by at most 2."""
+    for q in small_moduli():
+        assert 68 * q < 1 << 48 and (q << 9) < 1 << 50
+        xs = [0, 1, q - 1, q, 3 * q - 1, 68 * q - 1, (q << 9) - 1, (1 << 50) - 1]
+        xs += [k * q + d for k in (1, 2, 67, 255, 511) for d in (-1, 0, 1)]
+        xs += [RNG.getrandbits(50) for _ in range(2000)] + [RNG.randrange(68 * q) for _ in range(2000)]
+        for x in xs:
+            qe, r = red3_small(x, q)
+            assert 0 <= x // q - qe <= 2, (q, x)
+            assert r == x - qe * q and r < 3 * q and r % q == x % q
+
+
+def test_inverse_passes_with_approximate_products():
+    """The inverse passes' M schedule when the GS product lands in [0, 4q)
+    (2^32 < q < 2^41): every stage's inputs stay below its M (so a - b + M
+    never goes negative), and a pass ends below 2^(LOGS+1) q < 2^50."""
+    for q in small_moduli():
+        for logs in (6, 7, 8):
+            # row pass: words enter below q; stage 0 takes M = q, stage i > 0 M = q 2^(i+1)
+            bound = q
+            for lt in range(logs):
+                M = q if lt == 0 else q << (lt + 1)
+                assert bound <= M and M + bound <= M64
+                bound = max(2 * M, 4 * q)
+            assert bound <= q << (logs + 1) < 1 << 50
+            # column pass: words enter below 2q; stage i takes M = 2q 2^i
+            bound = 2 * q
+            for lt in range(logs):
+                M = (2 * q) << lt
+                assert bound <= M and M + bound <= M64
+                bound = max(2 * M, 4 * q)
+            assert bound <= q << (logs + 1) < 1 << 50
+            # and the approximate Shoup product takes any such word to [0, 4q)
+            for w in (1, q - 1, RNG.randrange(q)):
+                ws = shoup_const(w, q)
+                for b in (bound - 1, RNG.randrange(bound), (1 << 50) - 1):
+                    r = (b * w - approx_quotient(b, ws) * q) & M64
+                    assert r < 4 * q and r % q == (b * w) % q
