@@ -160,14 +160,17 @@ __device__ __forceinline__ u64 mul_shoup_lazy(u64 a, u64 w, u64 ws, u64 q) {
 // Cooley-Tukey butterfly (forward), lazy (Harvey): inputs and outputs in
 // [0, 4q) (every modulus is below 2^60, so 4q < 2^64);
 // (a, b) -> (a + w b, a - w b) mod q up to multiples of q.
-__device__ __forceinline__ void ct_bfly(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
-    u64 w, ws;
-    tw_at(tab, idx, w, ws);
+__device__ __forceinline__ void ct_bfly_w(u64& a, u64& b, u64 w, u64 ws, u64 q) {
     const u64 q2 = 2 * q;
     const u64 x = a >= q2 ? a - q2 : a;
     const u64 v = mul_shoup_lazy(b, w, ws, q);
     a = x + v;
     b = x - v + q2;
+}
+__device__ __forceinline__ void ct_bfly(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
+    u64 w, ws;
+    tw_at(tab, idx, w, ws);
+    ct_bfly_w(a, b, w, ws, q);
 }
 
 // Gentleman-Sande butterfly (inverse), lazy: inputs and outputs in [0, 2q);
@@ -230,17 +233,35 @@ __device__ __forceinline__ u64 mul_shoup_approx(u64 b, u64 w, u64 ws, u64 q) {
 }
 
 template <bool GROW>
-__device__ __forceinline__ void ct(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
+__device__ __forceinline__ void ct_w(u64& a, u64& b, u64 w, u64 ws, u64 q) {
     if constexpr (GROW) {
-        u64 w, ws;
-        tw_at(tab, idx, w, ws);
         const u64 v = mul_shoup_approx(b, w, ws, q);  // [0, 4q)
         b = a - v + 4 * q;
         a = a + v;
     } else {
-        ct_bfly(a, b, tab, idx, q);
+        ct_bfly_w(a, b, w, ws, q);
     }
 }
+template <bool GROW>
+__device__ __forceinline__ void ct(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
+    u64 w, ws;
+    tw_at(tab, idx, w, ws);
+    ct_w<GROW>(a, b, w, ws, q);
+}
+// A staged twiddle pair in shared memory.
+template <bool GROW>
+__device__ __forceinline__ void ct_s(u64& a, u64& b, const ulonglong2& t, u64 q) {
+    const ulonglong2 v = t;
+    ct_w<GROW>(a, b, v.x, v.y, q);
+}
+
+// 16-byte asynchronous copy global -> shared (both 16-byte aligned), L2 only.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const u32 d = (u32)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // GM = 0: reducing (gs_bfly); 1: growing, exact lazy Shoup product in [0, 2q);
 // 2: growing, approximate quotient (mul_shoup_approx) in [0, 4q) -- the
@@ -274,14 +295,16 @@ __device__ __forceinline__ u32 pad16(u32 i) { return i + (i >> 4); }
 // ------------------------------------------------------------------ forward, column pass
 // Global stages 0..LOGS-1 (m = 2^ss, twiddle psi^brv(m + r / 2t_r)).
 template <int LOGS, bool GROW>
-__device__ __forceinline__ void fwd_cols_stages(u64 (&x)[16], u64* sm, u32 u, u32 c, const ulonglong2* tw, u64 q) {
+// ts: the pass's twiddle pairs 0 .. S - 1, staged in shared memory (every
+// column of a limb uses the same S - 1 pairs).
+__device__ __forceinline__ void fwd_cols_stages(u64 (&x)[16], u64* sm, u32 u, u32 c, const ulonglong2* ts, u64 q) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
 #pragma unroll
     for (int ss = 0; ss < 4; ss++) {
         const int tv = 8 >> ss;
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & tv)) ct<GROW>(x[v], x[v + tv], tw, (1u << ss) + (v >> (4 - ss)), q);
+            if (!(v & tv)) ct_s<GROW>(x[v], x[v + tv], ts[(1u << ss) + (v >> (4 - ss))], q);
     }
 #pragma unroll
     for (int v = 0; v < 16; v++) sm[(u + TPL * v) * W + c] = x[v];
@@ -293,7 +316,7 @@ __device__ __forceinline__ void fwd_cols_stages(u64 (&x)[16], u64* sm, u32 u, u3
         const int t = S >> (ss + 1);
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & t)) ct<GROW>(x[v], x[v + t], tw, (1u << ss) + ((16 * u + v) >> (LOGS - ss)), q);
+            if (!(v & t)) ct_s<GROW>(x[v], x[v + t], ts[(1u << ss) + ((16 * u + v) >> (LOGS - ss))], q);
     }
 }
 
@@ -345,6 +368,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
                                                       const __grid_constant__ Jobs<FwdJob> jobs) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
     __shared__ u64 sm[S * W];
+    __shared__ __align__(16) ulonglong2 ts[S];
     constexpr u32 N = 1u << LOGN, C = N >> LOGS;
     const u32 c = threadIdx.x % W, u = threadIdx.x / W;
     const u32 col = blockIdx.x * W + c;
@@ -352,6 +376,9 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
     const ModC m = T.mods[J.mod];
     const u64 q = m.q;
     const ulonglong2* tw = T.psi + (size_t)J.mod * N;
+    // the S - 1 twiddle pairs of the column stages (indices 1 .. S - 1), copied while the words load
+    if (threadIdx.x < S) cp_async16(&ts[threadIdx.x], tw + threadIdx.x);
+    cp_async_commit();
     u64 x[16];
     if constexpr (BCONV) {
         // basis conversion (Eq. 3) of the thread's 16 words, staged through its
@@ -377,27 +404,37 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
 #pragma unroll
         for (int v = 0; v < 16; v++) x[v] = J.src[(size_t)(u + TPL * v) * C + col];
     }
+    cp_async_wait_all();
+    __syncthreads();
     // words enter below 4q; they leave below 4q (reducing) or 36q (growing: +4q per stage),
     // and the row pass ends below 68q < 2^64 (q < 2^57)
-    if (q < FWD_GROW_MAX) fwd_cols_stages<LOGS, true>(x, sm, u, c, tw, q);
-    else fwd_cols_stages<LOGS, false>(x, sm, u, c, tw, q);
+    if (q < FWD_GROW_MAX) fwd_cols_stages<LOGS, true>(x, sm, u, c, ts, q);
+    else fwd_cols_stages<LOGS, false>(x, sm, u, c, ts, q);
 #pragma unroll
     for (int v = 0; v < 16; v++) J.dst[(size_t)(16 * u + v) * C + col] = x[v];
 }
 
 // ------------------------------------------------------------------ forward, row pass
 // Global stages log_r..log_n-1 (m = 2^(log_r+ss), twiddle psi^brv(m + row 2^ss + x / 2t)).
+// The row pass's first round (stages 0-3) uses 15 twiddle pairs per row,
+// shared by the row's threads.  The kernel stages them in shared memory (t1,
+// slot 2^ss - 1 + j), copied asynchronously while the row's words load, so
+// that the round's butterflies do not wait on L2 stage by stage.  Rows are 15
+// pairs (240 bytes) apart: an odd number of 16-byte slots, so the rows of one
+// warp (2, 4 or 8) read different banks.  The second round's pairs (240 per
+// row, each used by one thread) are read from L2 as needed: staging those
+// too cost more (copies and 32 KB per CTA) than their latency.
+constexpr u32 T1_STRIDE = 15;
 template <int LOGS, bool GROW>
 __device__ __forceinline__ void fwd_rows_stages(u64 (&x)[16], u64* sr, u32 u, u32 row, u32 log_r,
-                                                const ulonglong2* tw, u64 q) {
+                                                const ulonglong2* tw, u64 q, const ulonglong2* t1) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16;
 #pragma unroll
     for (int ss = 0; ss < 4; ss++) {
         const int tv = 8 >> ss;
-        const u32 b0 = (1u << (log_r + ss)) + (row << ss);
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & tv)) ct<GROW>(x[v], x[v + tv], tw, b0 + (v >> (4 - ss)), q);
+            if (!(v & tv)) ct_s<GROW>(x[v], x[v + tv], t1[(1 << ss) - 1 + (v >> (4 - ss))], q);
     }
 #pragma unroll
     for (int v = 0; v < 16; v++) sr[pad16(u + TPL * v)] = x[v];
@@ -414,6 +451,17 @@ __device__ __forceinline__ void fwd_rows_stages(u64 (&x)[16], u64* sr, u32 u, u3
     }
 }
 
+// Issues the copies of a row's first-round twiddles into t1 (the caller commits and waits).
+template <int LOGS>
+__device__ __forceinline__ void fwd_rows_stage_twiddles(const ulonglong2* tw, u32 u, u32 row, u32 log_r,
+                                                        ulonglong2* t1) {
+    constexpr u32 TPL = (1u << LOGS) / 16;
+    for (u32 k = u; k < 15; k += TPL) {
+        const u32 ss = 31 - __clz(k + 1), j = k + 1 - (1u << ss);
+        cp_async16(&t1[k], tw + (1u << (log_r + ss)) + (row << ss) + j);
+    }
+}
+
 // The row pass of one limb in one arithmetic class (chosen once per block, so
 // that each class is compiled and register-allocated on its own):
 // AR = 0: reducing butterflies, words below 4q;
@@ -421,14 +469,16 @@ __device__ __forceinline__ void fwd_rows_stages(u64 (&x)[16], u64* sr, u32 u, u3
 // AR = 2: growing butterflies with 2^32 < q < 2^41, reduced by red3_small.
 template <int LOGN, int LOGS, bool SUBMUL, int AR>
 __device__ __forceinline__ void fwd_rows_limb(const FwdJob& J, const ModC& m, const ulonglong2* tw, u64* sr,
-                                              u32 u, u32 row) {
+                                              const ulonglong2* t1, u32 u, u32 row) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, log_r = LOGN - LOGS;
     const u64 q = m.q;
     const size_t base = (size_t)row * S;
     u64 x[16];
 #pragma unroll
     for (int v = 0; v < 16; v++) x[v] = J.dst[base + u + TPL * v];
-    fwd_rows_stages<LOGS, (AR > 0)>(x, sr, u, row, log_r, tw, q);
+    cp_async_wait_all();
+    __syncwarp();  // a row's threads are lanes of one warp
+    fwd_rows_stages<LOGS, (AR > 0)>(x, sr, u, row, log_r, tw, q, t1);
     __syncwarp();
 #pragma unroll
     for (int v = 0; v < 16; v++) sr[pad16(16 * u + v)] = x[v];
@@ -456,21 +506,45 @@ __device__ __forceinline__ void fwd_rows_limb(const FwdJob& J, const ModC& m, co
     }
 }
 
+// Shared memory of k_fwd_rows: the exchange rows, then t1 (38 KB at N = 2^16, 49 KB at 2^12).
+template <int LOGS>
+constexpr size_t fwd_rows_smem() {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
+    return (size_t)B * SP * 8 + (size_t)B * T1_STRIDE * 16;
+}
+
+// Three CTAs per SM (80 registers; measured faster than four at 64).
 template <int LOGN, int LOGS, bool SUBMUL>
-__global__ void __launch_bounds__(THREADS, 4) k_fwd_rows(const __grid_constant__ NttTables T,
+__global__ void __launch_bounds__(THREADS, 3) k_fwd_rows(const __grid_constant__ NttTables T,
                                                       const __grid_constant__ Jobs<FwdJob> jobs) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
-    __shared__ u64 sm[B * SP];
-    constexpr u32 N = 1u << LOGN;
+    constexpr u32 N = 1u << LOGN, log_r = LOGN - LOGS;
+    extern __shared__ __align__(16) u64 dsm[];
+    u64* sm = dsm;
+    ulonglong2* t1s = (ulonglong2*)(dsm + B * SP);
     const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
     const u32 row = blockIdx.x * B + rl;
     const FwdJob& J = jobs.j[blockIdx.y];
     const ModC m = T.mods[J.mod];
     const ulonglong2* tw = T.psi + (size_t)J.mod * N;
     u64* sr = sm + rl * SP;
-    if (small_q(m.q)) fwd_rows_limb<LOGN, LOGS, SUBMUL, 2>(J, m, tw, sr, u, row);
-    else if (m.q < FWD_GROW_MAX) fwd_rows_limb<LOGN, LOGS, SUBMUL, 1>(J, m, tw, sr, u, row);
-    else fwd_rows_limb<LOGN, LOGS, SUBMUL, 0>(J, m, tw, sr, u, row);
+    ulonglong2* t1 = t1s + rl * T1_STRIDE;
+    fwd_rows_stage_twiddles<LOGS>(tw, u, row, log_r, t1);
+    cp_async_commit();
+    if (small_q(m.q)) fwd_rows_limb<LOGN, LOGS, SUBMUL, 2>(J, m, tw, sr, t1, u, row);
+    else if (m.q < FWD_GROW_MAX) fwd_rows_limb<LOGN, LOGS, SUBMUL, 1>(J, m, tw, sr, t1, u, row);
+    else fwd_rows_limb<LOGN, LOGS, SUBMUL, 0>(J, m, tw, sr, t1, u, row);
+}
+
+// Sets a kernel's dynamic shared memory limit once per device.
+template <typename K>
+void smem_limit(K kernel, size_t bytes, std::atomic<uint64_t>& done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;  // the launch reports it
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+        done.fetch_or(bit, std::memory_order_release);
 }
 
 // ------------------------------------------------------------------ inverse, row pass
@@ -676,8 +750,15 @@ void fwd_impl(const NttTables& T, const Jobs<FwdJob>& p, int n, bool bconv, bool
     }
     {
         ProfScope ps(K_FWD_ROWS, st, 0, half * LC);
-        if (submul) k_fwd_rows<LR + LC, LC, true><<<g2, THREADS, 0, st>>>(T, p);
-        else k_fwd_rows<LR + LC, LC, false><<<g2, THREADS, 0, st>>>(T, p);
+        constexpr size_t sm = fwd_rows_smem<LC>();
+        static std::atomic<uint64_t> lim_t{0}, lim_f{0};
+        if (submul) {
+            smem_limit(k_fwd_rows<LR + LC, LC, true>, sm, lim_t);
+            k_fwd_rows<LR + LC, LC, true><<<g2, THREADS, sm, st>>>(T, p);
+        } else {
+            smem_limit(k_fwd_rows<LR + LC, LC, false>, sm, lim_f);
+            k_fwd_rows<LR + LC, LC, false><<<g2, THREADS, sm, st>>>(T, p);
+        }
     }
 }
 
