@@ -175,13 +175,16 @@ __device__ __forceinline__ void ct_bfly(u64& a, u64& b, const ulonglong2* tab, u
 
 // Gentleman-Sande butterfly (inverse), lazy: inputs and outputs in [0, 2q);
 // (a, b) -> (a + b, (a - b) w) mod q up to multiples of q.
-__device__ __forceinline__ void gs_bfly(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
-    u64 w, ws;
-    tw_at(tab, idx, w, ws);
+__device__ __forceinline__ void gs_bfly_w(u64& a, u64& b, u64 w, u64 ws, u64 q) {
     const u64 q2 = 2 * q;
     const u64 s = a + b;
     b = mul_shoup_lazy(a - b + q2, w, ws, q);
     a = s >= q2 ? s - q2 : s;
+}
+__device__ __forceinline__ void gs_bfly(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
+    u64 w, ws;
+    tw_at(tab, idx, w, ws);
+    gs_bfly_w(a, b, w, ws, q);
 }
 
 // [0, 4q) -> [0, q)
@@ -267,16 +270,26 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // 2: growing, approximate quotient (mul_shoup_approx) in [0, 4q) -- the
 // caller's M then doubles from 4q on (see the inverse passes).
 template <int GM>
-__device__ __forceinline__ void gs(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q, u64 M) {
+__device__ __forceinline__ void gs_w(u64& a, u64& b, u64 w, u64 ws, u64 q, u64 M) {
     if constexpr (GM > 0) {
-        u64 w, ws;
-        tw_at(tab, idx, w, ws);
         const u64 s = a + b;
         b = GM == 2 ? mul_shoup_approx(a - b + M, w, ws, q) : mul_shoup_lazy(a - b + M, w, ws, q);
         a = s;
     } else {
-        gs_bfly(a, b, tab, idx, q);
+        gs_bfly_w(a, b, w, ws, q);
     }
+}
+template <int GM>
+__device__ __forceinline__ void gs(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q, u64 M) {
+    u64 w, ws;
+    tw_at(tab, idx, w, ws);
+    gs_w<GM>(a, b, w, ws, q, M);
+}
+// With a staged twiddle pair in shared memory.
+template <int GM>
+__device__ __forceinline__ void gs_s(u64& a, u64& b, const ulonglong2& t, u64 q, u64 M) {
+    const ulonglong2 v = t;
+    gs_w<GM>(a, b, v.x, v.y, q, M);
 }
 
 // Every pass works on "lines" of S = 2^LOGS words (a column of the R x C
@@ -643,8 +656,9 @@ __global__ void __launch_bounds__(THREADS, 3) k_inv_rows(const __grid_constant__
 // then the scaling by c (N^-1 and any per-limb constant).
 // Growing forms: words enter below 2q; the i-th stage of the pass takes M = 2q 2^i,
 // which also bounds the [0, 4q) products of GM = 2 (outputs below 2^(LOGS+1) q).
+// ts: the pass's twiddle pairs 0 .. S - 1, staged in shared memory.
 template <int LOGS, int GM>
-__device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u32 c, const ulonglong2* tw, u64 q) {
+__device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u32 c, const ulonglong2* ts, u64 q) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
 #pragma unroll
     for (int lt = 0; lt < LOGS - 4; lt++) {
@@ -652,7 +666,7 @@ __device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u3
         const u64 M = (2 * q) << lt;
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & t)) gs<GM>(x[v], x[v + t], tw, (S >> (lt + 1)) + ((16 * u + v) >> (lt + 1)), q, M);
+            if (!(v & t)) gs_s<GM>(x[v], x[v + t], ts[(S >> (lt + 1)) + ((16 * u + v) >> (lt + 1))], q, M);
     }
 #pragma unroll
     for (int v = 0; v < 16; v++) sm[(16 * u + v) * W + c] = x[v];
@@ -665,7 +679,7 @@ __device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u3
         const u64 M = (2 * q) << lt;
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & (1 << k))) gs<GM>(x[v], x[v + (1 << k)], tw, (S >> (lt + 1)) + (v >> (k + 1)), q, M);
+            if (!(v & (1 << k))) gs_s<GM>(x[v], x[v + (1 << k)], ts[(S >> (lt + 1)) + (v >> (k + 1))], q, M);
     }
 }
 
@@ -673,13 +687,15 @@ __device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u3
 // scaling by c: mul_shoup reduces any 64-bit word fully; the approximate
 // product (GM = 2) takes it to [0, 4q) first.
 template <int LOGN, int LOGS, int GM>
-__device__ __forceinline__ void inv_cols_limb(const InvJob& J, u64 q, const ulonglong2* tw, u64* sm, u32 u, u32 c,
+__device__ __forceinline__ void inv_cols_limb(const InvJob& J, u64 q, const ulonglong2* ts, u64* sm, u32 u, u32 c,
                                               u32 col) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, C = (1u << LOGN) >> LOGS;
     u64 x[16];
 #pragma unroll
     for (int v = 0; v < 16; v++) x[v] = J.tmp[(size_t)(16 * u + v) * C + col];
-    inv_cols_stages<LOGS, GM>(x, sm, u, c, tw, q);
+    cp_async_wait_all();
+    __syncthreads();
+    inv_cols_stages<LOGS, GM>(x, sm, u, c, ts, q);
 #pragma unroll
     for (int v = 0; v < 16; v++) {
         u64 y;
@@ -694,15 +710,19 @@ __global__ void __launch_bounds__(THREADS, 3) k_inv_cols(const __grid_constant__
                                                       const __grid_constant__ Jobs<InvJob> jobs) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
     __shared__ u64 sm[S * W];
+    __shared__ __align__(16) ulonglong2 ts[S];
     constexpr u32 N = 1u << LOGN;
     const u32 c = threadIdx.x % W, u = threadIdx.x / W;
     const u32 col = blockIdx.x * W + c;
     const InvJob& J = jobs.j[blockIdx.y];
     const u64 q = T.mods[J.mod].q;
     const ulonglong2* tw = T.ipsi + (size_t)J.mod * N;
-    if (small_q(q)) inv_cols_limb<LOGN, LOGS, 2>(J, q, tw, sm, u, c, col);
-    else if (q < INV_GROW_MAX) inv_cols_limb<LOGN, LOGS, 1>(J, q, tw, sm, u, c, col);
-    else inv_cols_limb<LOGN, LOGS, 0>(J, q, tw, sm, u, c, col);
+    // the S - 1 twiddle pairs of the column stages (indices 1 .. S - 1), copied while the words load
+    if (threadIdx.x < S) cp_async16(&ts[threadIdx.x], tw + threadIdx.x);
+    cp_async_commit();
+    if (small_q(q)) inv_cols_limb<LOGN, LOGS, 2>(J, q, ts, sm, u, c, col);
+    else if (q < INV_GROW_MAX) inv_cols_limb<LOGN, LOGS, 1>(J, q, ts, sm, u, c, col);
+    else inv_cols_limb<LOGN, LOGS, 0>(J, q, ts, sm, u, c, col);
 }
 
 __global__ void k_automorphism(const u64* __restrict__ in, u64* __restrict__ out, u32 gal, u32 log_n) {
