@@ -495,6 +495,15 @@ __device__ __forceinline__ void fwd_rows_limb(const FwdJob& J, const ModC& m, co
     __syncwarp();
 #pragma unroll
     for (int v = 0; v < 16; v++) sr[pad16(16 * u + v)] = x[v];
+    // The ModDown tail's x words, every one loaded before this thread's first
+    // store: an output limb may be its input limb (each thread reads and
+    // writes only its own 16 words), so loads interleaved with the stores
+    // could not be moved ahead of them and would each wait a full round trip.
+    u64 sx[SUBMUL ? 16 : 1];
+    if constexpr (SUBMUL) {
+#pragma unroll
+        for (int v = 0; v < 16; v++) sx[v] = J.subx[base + u + TPL * v];
+    }
     __syncwarp();
 #pragma unroll
     for (int v = 0; v < 16; v++) {
@@ -512,7 +521,7 @@ __device__ __forceinline__ void fwd_rows_limb(const FwdJob& J, const ModC& m, co
             val = canon4(y, q);
         }
         if constexpr (SUBMUL) {
-            J.subout[base + xi] = mul_shoup(sub_mod(J.subx[base + xi], val, q), J.c, J.c_sh, q);
+            J.subout[base + xi] = mul_shoup(sub_mod(sx[v], val, q), J.c, J.c_sh, q);
         } else {
             J.dst[base + xi] = val;
         }
