@@ -496,9 +496,9 @@ __device__ __forceinline__ void fwd_rows_limb(const FwdJob& J, const ModC& m, co
 #pragma unroll
     for (int v = 0; v < 16; v++) sr[pad16(16 * u + v)] = x[v];
     // The ModDown tail's x words, every one loaded before this thread's first
-    // store: an output limb may be its input limb (each thread reads and
-    // writes only its own 16 words), so loads interleaved with the stores
-    // could not be moved ahead of them and would each wait a full round trip.
+    // store.  The compiler cannot tell that the output limbs never overlap
+    // them, so loads interleaved with the stores could not move ahead of them
+    // and would each wait a full round trip.
     u64 sx[SUBMUL ? 16 : 1];
     if constexpr (SUBMUL) {
 #pragma unroll
