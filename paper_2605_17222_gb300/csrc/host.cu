@@ -383,18 +383,16 @@ void op_decompose_batch(ckks_ctx* C, u32 level, const std::vector<const u64*>& c
                                     C->gmod(level, t), n | (small ? 1u << 16 : 0u)});
             }
         }
-    }
-    launch_fwd_ntt(C->T, fj.data(), (int)fj.size(), st);
-    // each digit's own limbs are the (gathered) input limbs: one copy launch for all of them
-    std::vector<AddJob> cj;
-    cj.reserve((size_t)cnt * level);
-    for (u32 p = 0; p < cnt; p++)
+        // each digit's own limbs are the (gathered) input limbs: copy jobs in the same launch, after
+        // the polynomial's transforms, so that they fill the transforms' last wave
         for (u32 b = 0; b < beta; b++) {
             const u32 first = b * C->alpha, n = std::min(C->alpha, level - first);
             for (u32 j = first; j < first + n; j++)
-                cj.push_back(AddJob{cs[p] + (size_t)j * N, nullptr, digits[p] + ((size_t)b * ext + j) * N, j, 0});
+                fj.push_back(FwdJob{cs[p] + (size_t)j * N, digits[p] + ((size_t)b * ext + j) * N, nullptr, nullptr,
+                                    nullptr, gal, 0, j, FWD_COPY});
         }
-    launch_add_gather((const ModC*)C->d_mods.p, cj.data(), (int)cj.size(), gal, 0, C->log_n, st);
+    }
+    launch_fwd_ntt(C->T, fj.data(), (int)fj.size(), st);
 }
 
 void op_decompose(ckks_ctx* C, u32 level, const u64* c, u32 gal, u64* digits, u64* Y, cudaStream_t st) {

@@ -24,6 +24,10 @@ struct NttTables {
 //   pass 2 store: subout == nullptr -> dst[x] = X;
 //                 otherwise subout[x] = (subx[x] - X) * c mod q        (ModDown tail, Eq. 4)
 // Pass 1 writes dst; pass 2 runs in place on dst.
+// FwdJob::nsrc bit 17: a copy job, dst[x] = src[x -> x^gal] with gal in c
+// (0: plain copy) and no transform, for the limbs a Decompose passes through
+// unchanged; it rides in the same launch as the transforms.
+constexpr u32 FWD_COPY = 1u << 17;
 struct FwdJob {
     const u64* src;
     u64* dst;

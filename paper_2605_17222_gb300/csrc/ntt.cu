@@ -137,7 +137,7 @@ ProfScope::~ProfScope() {
 
 namespace {
 
-constexpr int MAXJ = 240;  // jobs per launch (kernel parameters are passed by value)
+constexpr int MAXJ = 480;  // jobs per launch (passed by value: 480 forward jobs are 30 KB of the 32 KB kernel parameters)
 constexpr int THREADS = 256;
 
 template <typename J>
@@ -389,6 +389,18 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
     const ModC m = T.mods[J.mod];
     const u64 q = m.q;
     const ulonglong2* tw = T.psi + (size_t)J.mod * N;
+    if (J.nsrc & FWD_COPY) {  // a pass-through limb: the block copies its columns (every word loaded first)
+        const u32 gal = (u32)J.c;
+        u64 y[16];
+#pragma unroll
+        for (int v = 0; v < 16; v++) {
+            const u32 idx = (u + TPL * v) * C + col;
+            y[v] = J.src[gal ? auto_src(idx, gal, LOGN) : idx];
+        }
+#pragma unroll
+        for (int v = 0; v < 16; v++) J.dst[(size_t)(u + TPL * v) * C + col] = y[v];
+        return;
+    }
     // the S - 1 twiddle pairs of the column stages (indices 1 .. S - 1), copied while the words load
     if (threadIdx.x < S) cp_async16(&ts[threadIdx.x], tw + threadIdx.x);
     cp_async_commit();
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
         // basis conversion (Eq. 3) of the thread's 16 words, staged through its
         // own slots of the exchange buffer so that this part stays a compact loop
         const u32 ns = J.nsrc & 0xFFFFu;
-        const bool small = (J.nsrc >> 16) && q > (1ull << 32) && q < (1ull << 41);
+        const bool small = ((J.nsrc >> 16) & 1u) && q > (1ull << 32) && q < (1ull << 41);
         if (ns == 4 && small) bconv_words<LOGS, 4, true>(sm, J, u, c, col, N, C, m);
         else if (ns == 4) bconv_words<LOGS, 4, false>(sm, J, u, c, col, N, C, m);
         else if (ns == 5) bconv_words<LOGS, 5, false>(sm, J, u, c, col, N, C, m);
@@ -547,6 +559,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_fwd_rows(const __grid_constant__
     const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
     const u32 row = blockIdx.x * B + rl;
     const FwdJob& J = jobs.j[blockIdx.y];
+    if (J.nsrc & FWD_COPY) return;  // copied by the column pass
     const ModC m = T.mods[J.mod];
     const ulonglong2* tw = T.psi + (size_t)J.mod * N;
     u64* sr = sm + rl * SP;
@@ -768,10 +781,13 @@ template <int LR, int LC>
 void fwd_impl(const NttTables& T, const Jobs<FwdJob>& p, int n, bool bconv, bool submul, cudaStream_t st) {
     const u32 N = 1u << T.log_n;
     const dim3 g1((N >> LR) / (THREADS / ((1u << LR) / 16)), n), g2((N >> LC) / (THREADS / ((1u << LC) / 16)), n);
-    const double half = (double)n * (N / 2);  // butterflies per stage over the launch's limbs
+    int nt = 0;  // transformed limbs (copy jobs aside)
+    for (int i = 0; i < n; i++) nt += (p.j[i].nsrc & FWD_COPY) ? 0 : 1;
+    const double half = (double)nt * (N / 2);  // butterflies per stage over the launch's limbs
     double bconv_macs = 0;
     if (bconv)
-        for (int i = 0; i < n; i++) bconv_macs += (double)(p.j[i].nsrc & 0xFFFFu) * N;
+        for (int i = 0; i < n; i++)
+            if (!(p.j[i].nsrc & FWD_COPY)) bconv_macs += (double)(p.j[i].nsrc & 0xFFFFu) * N;
     {
         ProfScope ps(K_FWD_COLS, st, bconv_macs, half * LR);
         if (bconv) k_fwd_cols<LR + LC, LR, true><<<g1, THREADS, 0, st>>>(T, p);
@@ -873,7 +889,14 @@ __global__ void __launch_bounds__(PROBE_THREADS, 4) k_probe_bfly(const ulonglong
 
 void launch_fwd_ntt(const NttTables& T, const FwdJob* jobs, int njobs, cudaStream_t st) {
     if (njobs <= 0) return;
-    const bool bconv = (jobs[0].nsrc & 0xFFFFu) > 0, submul = jobs[0].subout != nullptr;
+    // every transform job of a launch is of one kind (copy jobs may join any)
+    bool bconv = false, submul = false;
+    for (int i = 0; i < njobs; i++)
+        if (!(jobs[i].nsrc & FWD_COPY)) {
+            bconv = (jobs[i].nsrc & 0xFFFFu) > 0;
+            submul = jobs[i].subout != nullptr;
+            break;
+        }
     for_chunks(jobs, njobs, [&](const Jobs<FwdJob>& p, int n) {
         NTT_DISPATCH(fwd_impl, bconv, submul);
         count_launch(2);
