@@ -173,20 +173,6 @@ __device__ __forceinline__ void ct_bfly(u64& a, u64& b, const ulonglong2* tab, u
     ct_bfly_w(a, b, w, ws, q);
 }
 
-// Gentleman-Sande butterfly (inverse), lazy: inputs and outputs in [0, 2q);
-// (a, b) -> (a + b, (a - b) w) mod q up to multiples of q.
-__device__ __forceinline__ void gs_bfly_w(u64& a, u64& b, u64 w, u64 ws, u64 q) {
-    const u64 q2 = 2 * q;
-    const u64 s = a + b;
-    b = mul_shoup_lazy(a - b + q2, w, ws, q);
-    a = s >= q2 ? s - q2 : s;
-}
-__device__ __forceinline__ void gs_bfly(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
-    u64 w, ws;
-    tw_at(tab, idx, w, ws);
-    gs_bfly_w(a, b, w, ws, q);
-}
-
 // [0, 4q) -> [0, q)
 __device__ __forceinline__ u64 canon4(u64 x, u64 q) {
     x = x >= 2 * q ? x - 2 * q : x;
@@ -216,13 +202,9 @@ __device__ __forceinline__ bool small_q(u64 q) { return q > (1ull << 32) && q < 
 //       are both below B + 4q.  The log N <= 16 stages of a forward transform
 //       from [0, 4q) (a lazily reduced basis conversion) stay below 68q, below
 //       2^64 for q < 2^57.
-//   GS: if both inputs are below M (a multiple of q), (a + b, (a - b + M) w
-//       mod q) are below 2M.  The <= 8 stages of one pass from [0, B) stay
-//       below 2^8 B; a pass starts from [0, q) (row) or [0, 2q) (column), so
-//       everything stays below 2^9 q < 2^64 for q < 2^55.
 // Wider moduli (the 60-bit special primes) take the reducing butterflies.
+// The inverse transform keeps one lazy form for every modulus (gs_w).
 constexpr u64 FWD_GROW_MAX = 1ull << 57;
-constexpr u64 INV_GROW_MAX = 1ull << 55;
 
 // b w mod q up to 4q, for any b < 2^64 (w < q, ws = floor(w 2^64 / q)).  Of
 // the four 32 x 32 partial products of b ws the quotient estimate keeps the
@@ -266,30 +248,28 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// GM = 0: reducing (gs_bfly); 1: growing, exact lazy Shoup product in [0, 2q);
-// 2: growing, approximate quotient (mul_shoup_approx) in [0, 4q) -- the
-// caller's M then doubles from 4q on (see the inverse passes).
-template <int GM>
-__device__ __forceinline__ void gs_w(u64& a, u64& b, u64 w, u64 ws, u64 q, u64 M) {
-    if constexpr (GM > 0) {
-        const u64 s = a + b;
-        b = GM == 2 ? mul_shoup_approx(a - b + M, w, ws, q) : mul_shoup_lazy(a - b + M, w, ws, q);
-        a = s;
-    } else {
-        gs_bfly_w(a, b, w, ws, q);
-    }
+// Gentleman-Sande butterfly (inverse), lazy (Harvey), for every modulus below
+// 2^62: inputs and outputs in [0, 2q); (a, b) -> (a + b, (a - b) w) mod q up
+// to multiples of q (the lazy Shoup product of a word below 4q is in [0, 2q)).
+// One form for all moduli keeps the passes to a single body: a launch of one
+// or two CTAs per SM fetches a body's fully unrolled code from L2 line by
+// line, and the special primes' small launches (ModDown sources) would
+// otherwise run a body that the big launches never warm.
+__device__ __forceinline__ void gs_w(u64& a, u64& b, u64 w, u64 ws, u64 q) {
+    const u64 q2 = 2 * q;
+    const u64 s = a + b;
+    b = mul_shoup_lazy(a - b + q2, w, ws, q);
+    a = s >= q2 ? s - q2 : s;
 }
-template <int GM>
-__device__ __forceinline__ void gs(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q, u64 M) {
+__device__ __forceinline__ void gs(u64& a, u64& b, const ulonglong2* tab, u32 idx, u64 q) {
     u64 w, ws;
     tw_at(tab, idx, w, ws);
-    gs_w<GM>(a, b, w, ws, q, M);
+    gs_w(a, b, w, ws, q);
 }
 // With a staged twiddle pair in shared memory.
-template <int GM>
-__device__ __forceinline__ void gs_s(u64& a, u64& b, const ulonglong2& t, u64 q, u64 M) {
+__device__ __forceinline__ void gs_s(u64& a, u64& b, const ulonglong2& t, u64 q) {
     const ulonglong2 v = t;
-    gs_w<GM>(a, b, v.x, v.y, q, M);
+    gs_w(a, b, v.x, v.y, q);
 }
 
 // Every pass works on "lines" of S = 2^LOGS words (a column of the R x C
@@ -492,6 +472,8 @@ __device__ __forceinline__ void fwd_rows_stage_twiddles(const ulonglong2* tw, u3
 // AR = 0: reducing butterflies, words below 4q;
 // AR = 1: growing butterflies, words below 68q, reduced by red2;
 // AR = 2: growing butterflies with 2^32 < q < 2^41, reduced by red3_small.
+// Every class occurs in the big Decompose launches (special-prime, first-prime
+// and 40-bit targets), so none runs cold in a small launch.
 template <int LOGN, int LOGS, bool SUBMUL, int AR>
 __device__ __forceinline__ void fwd_rows_limb(const FwdJob& J, const ModC& m, const ulonglong2* tw, u64* sr,
                                               const ulonglong2* t1, u32 u, u32 row) {
@@ -584,15 +566,8 @@ void smem_limit(K kernel, size_t bytes, std::atomic<uint64_t>& done) {
 
 // ------------------------------------------------------------------ inverse, row pass
 // GS stages with half-width t = 1..S/2 (m = N/2t, twiddle psi^-brv(m + row S/2t + x/2t)).
-// Growing forms: words enter below q.  GM = 1: the i-th stage of the pass takes
-// M = q 2^i (outputs below 2^LOGS q).  GM = 2 (products in [0, 4q)): stage 0
-// takes M = q and leaves words below 4q, stage i > 0 takes M = q 2^(i+1)
-// (outputs below 2^(LOGS+1) q).
-template <int GM>
-__device__ __forceinline__ u64 inv_rows_m(u64 q, int lt) {
-    return GM == 2 ? (lt == 0 ? q : q << (lt + 1)) : q << lt;
-}
-template <int LOGS, int GM>
+// Words enter below q (canonical) and stay in [0, 2q).
+template <int LOGS>
 __device__ __forceinline__ void inv_rows_stages(u64 (&x)[16], u64* sr, u32 u, u32 row, u32 N,
                                                 const ulonglong2* tw, u64 q) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16;
@@ -600,10 +575,9 @@ __device__ __forceinline__ void inv_rows_stages(u64 (&x)[16], u64* sr, u32 u, u3
     for (int lt = 0; lt < LOGS - 4; lt++) {  // t = 1 .. TPL/2
         const int t = 1 << lt;
         const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
-        const u64 M = inv_rows_m<GM>(q, lt);
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & t)) gs<GM>(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (lt + 1)), q, M);
+            if (!(v & t)) gs(x[v], x[v + t], tw, b0 + ((16 * u + v) >> (lt + 1)), q);
     }
     __syncwarp();
 #pragma unroll
@@ -615,19 +589,24 @@ __device__ __forceinline__ void inv_rows_stages(u64 (&x)[16], u64* sr, u32 u, u3
     for (int k = 0; k < 4; k++) {  // t = TPL * 2^k
         const int lt = (LOGS - 4) + k;
         const u32 b0 = (N >> (lt + 1)) + row * (S >> (lt + 1));
-        const u64 M = inv_rows_m<GM>(q, lt);
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & (1 << k))) gs<GM>(x[v], x[v + (1 << k)], tw, b0 + (v >> (k + 1)), q, M);
+            if (!(v & (1 << k))) gs(x[v], x[v + (1 << k)], tw, b0 + (v >> (k + 1)), q);
     }
 }
 
-// The inverse row pass of one limb in one arithmetic class GM (gs above).
-template <int LOGN, int LOGS, bool GATHER, int GM>
-__device__ __forceinline__ void inv_rows_limb(const InvJob& J, const ModC& m, const ulonglong2* tw, u64* sr,
-                                              u32 u, u32 row) {
-    constexpr u32 S = 1u << LOGS, TPL = S / 16, N = 1u << LOGN;
-    const u64 q = m.q;
+template <int LOGN, int LOGS, bool GATHER>
+__global__ void __launch_bounds__(THREADS, 3) k_inv_rows(const __grid_constant__ NttTables T,
+                                                      const __grid_constant__ Jobs<InvJob> jobs) {
+    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
+    __shared__ u64 sm[B * SP];
+    constexpr u32 N = 1u << LOGN;
+    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
+    const u32 row = blockIdx.x * B + rl;
+    const InvJob& J = jobs.j[blockIdx.y];
+    const u64 q = T.mods[J.mod].q;
+    const ulonglong2* tw = T.ipsi + (size_t)J.mod * N;
+    u64* sr = sm + rl * SP;
     const size_t base = (size_t)row * S;
     u64 x[16];
 #pragma unroll
@@ -641,54 +620,24 @@ __device__ __forceinline__ void inv_rows_limb(const InvJob& J, const ModC& m, co
     __syncwarp();
 #pragma unroll
     for (int v = 0; v < 16; v++) x[v] = sr[pad16(16 * u + v)];
-    inv_rows_stages<LOGS, GM>(x, sr, u, row, N, tw, q);
-    if constexpr (GM == 2) {
-#pragma unroll
-        for (int v = 0; v < 16; v++) {  // below 2^(LOGS+1) q <= 2^50 -> [0, 3q) -> [0, 2q)
-            const u64 r = red3_small(x[v], q, (u32)m.mu_hi);
-            x[v] = r >= 2 * q ? r - 2 * q : r;
-        }
-    } else if constexpr (GM == 1) {
-#pragma unroll
-        for (int v = 0; v < 16; v++) x[v] = red2(x[v], q, m.mu_hi);  // below 2^8 q -> [0, 2q)
-    }  // GM == 0 stays in [0, 2q)
+    inv_rows_stages<LOGS>(x, sr, u, row, N, tw, q);  // [0, 2q)
 #pragma unroll
     for (int v = 0; v < 16; v++) J.tmp[base + u + TPL * v] = x[v];
 }
 
-template <int LOGN, int LOGS, bool GATHER>
-__global__ void __launch_bounds__(THREADS, 3) k_inv_rows(const __grid_constant__ NttTables T,
-                                                      const __grid_constant__ Jobs<InvJob> jobs) {
-    constexpr u32 S = 1u << LOGS, TPL = S / 16, B = THREADS / TPL, SP = S + S / 16;
-    __shared__ u64 sm[B * SP];
-    constexpr u32 N = 1u << LOGN;
-    const u32 u = threadIdx.x % TPL, rl = threadIdx.x / TPL;
-    const u32 row = blockIdx.x * B + rl;
-    const InvJob& J = jobs.j[blockIdx.y];
-    const ModC m = T.mods[J.mod];
-    const ulonglong2* tw = T.ipsi + (size_t)J.mod * N;
-    u64* sr = sm + rl * SP;
-    if (small_q(m.q)) inv_rows_limb<LOGN, LOGS, GATHER, 2>(J, m, tw, sr, u, row);
-    else if (m.q < INV_GROW_MAX) inv_rows_limb<LOGN, LOGS, GATHER, 1>(J, m, tw, sr, u, row);
-    else inv_rows_limb<LOGN, LOGS, GATHER, 0>(J, m, tw, sr, u, row);
-}
-
 // ------------------------------------------------------------------ inverse, column pass
 // GS stages with half-width C*t_r, t_r = 1..S/2 (m = S/2t_r, twiddle psi^-brv(m + r/2t_r)),
-// then the scaling by c (N^-1 and any per-limb constant).
-// Growing forms: words enter below 2q; the i-th stage of the pass takes M = 2q 2^i,
-// which also bounds the [0, 4q) products of GM = 2 (outputs below 2^(LOGS+1) q).
+// then the scaling by c (N^-1 and any per-limb constant).  Words enter and stay in [0, 2q).
 // ts: the pass's twiddle pairs 0 .. S - 1, staged in shared memory.
-template <int LOGS, int GM>
+template <int LOGS>
 __device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u32 c, const ulonglong2* ts, u64 q) {
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
 #pragma unroll
     for (int lt = 0; lt < LOGS - 4; lt++) {
         const int t = 1 << lt;
-        const u64 M = (2 * q) << lt;
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & t)) gs_s<GM>(x[v], x[v + t], ts[(S >> (lt + 1)) + ((16 * u + v) >> (lt + 1))], q, M);
+            if (!(v & t)) gs_s(x[v], x[v + t], ts[(S >> (lt + 1)) + ((16 * u + v) >> (lt + 1))], q);
     }
 #pragma unroll
     for (int v = 0; v < 16; v++) sm[(16 * u + v) * W + c] = x[v];
@@ -698,32 +647,9 @@ __device__ __forceinline__ void inv_cols_stages(u64 (&x)[16], u64* sm, u32 u, u3
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const int lt = (LOGS - 4) + k;
-        const u64 M = (2 * q) << lt;
 #pragma unroll
         for (int v = 0; v < 16; v++)
-            if (!(v & (1 << k))) gs_s<GM>(x[v], x[v + (1 << k)], ts[(S >> (lt + 1)) + (v >> (k + 1))], q, M);
-    }
-}
-
-// The inverse column pass of one limb in one arithmetic class GM, then the
-// scaling by c: mul_shoup reduces any 64-bit word fully; the approximate
-// product (GM = 2) takes it to [0, 4q) first.
-template <int LOGN, int LOGS, int GM>
-__device__ __forceinline__ void inv_cols_limb(const InvJob& J, u64 q, const ulonglong2* ts, u64* sm, u32 u, u32 c,
-                                              u32 col) {
-    constexpr u32 S = 1u << LOGS, TPL = S / 16, C = (1u << LOGN) >> LOGS;
-    u64 x[16];
-#pragma unroll
-    for (int v = 0; v < 16; v++) x[v] = J.tmp[(size_t)(16 * u + v) * C + col];
-    cp_async_wait_all();
-    __syncthreads();
-    inv_cols_stages<LOGS, GM>(x, sm, u, c, ts, q);
-#pragma unroll
-    for (int v = 0; v < 16; v++) {
-        u64 y;
-        if constexpr (GM == 2) y = canon4(mul_shoup_approx(x[v], J.c, J.c_sh, q), q);
-        else y = mul_shoup(x[v], J.c, J.c_sh, q);
-        J.dst[(size_t)(u + TPL * v) * C + col] = y;
+            if (!(v & (1 << k))) gs_s(x[v], x[v + (1 << k)], ts[(S >> (lt + 1)) + (v >> (k + 1))], q);
     }
 }
 
@@ -733,7 +659,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_inv_cols(const __grid_constant__
     constexpr u32 S = 1u << LOGS, TPL = S / 16, W = THREADS / TPL;
     __shared__ u64 sm[S * W];
     __shared__ __align__(16) ulonglong2 ts[S];
-    constexpr u32 N = 1u << LOGN;
+    constexpr u32 N = 1u << LOGN, C = N >> LOGS;
     const u32 c = threadIdx.x % W, u = threadIdx.x / W;
     const u32 col = blockIdx.x * W + c;
     const InvJob& J = jobs.j[blockIdx.y];
@@ -742,9 +668,15 @@ __global__ void __launch_bounds__(THREADS, 3) k_inv_cols(const __grid_constant__
     // the S - 1 twiddle pairs of the column stages (indices 1 .. S - 1), copied while the words load
     if (threadIdx.x < S) cp_async16(&ts[threadIdx.x], tw + threadIdx.x);
     cp_async_commit();
-    if (small_q(q)) inv_cols_limb<LOGN, LOGS, 2>(J, q, ts, sm, u, c, col);
-    else if (q < INV_GROW_MAX) inv_cols_limb<LOGN, LOGS, 1>(J, q, ts, sm, u, c, col);
-    else inv_cols_limb<LOGN, LOGS, 0>(J, q, ts, sm, u, c, col);
+    u64 x[16];
+#pragma unroll
+    for (int v = 0; v < 16; v++) x[v] = J.tmp[(size_t)(16 * u + v) * C + col];
+    cp_async_wait_all();
+    __syncthreads();
+    inv_cols_stages<LOGS>(x, sm, u, c, ts, q);
+    // the scaling: mul_shoup reduces any 64-bit word fully
+#pragma unroll
+    for (int v = 0; v < 16; v++) J.dst[(size_t)(u + TPL * v) * C + col] = mul_shoup(x[v], J.c, J.c_sh, q);
 }
 
 __global__ void k_automorphism(const u64* __restrict__ in, u64* __restrict__ out, u32 gal, u32 log_n) {

@@ -5,15 +5,16 @@ its comment claims, so that a change to either side has something to fail.
 
   * the three-product Shoup quotient of the growing forward butterflies is at
     most 2 below floor(b ws / 2^64), so the remainder lies in [0, 4q);
-  * the growing butterflies' word bounds (68q forward from [0, 4q), 2^9 q per
-    inverse pass from [0, 2q)) stay below 2^64 for the moduli that take them;
+  * the growing forward butterflies' word bound (68q from [0, 4q)) stays
+    below 2^64 for the moduli that take them;
   * K6's fold of a middle-layer sum x = sum_b d_b k_b + A (beta <= 8, q < 2^41)
     is below 2^64, congruent to x mod q, and 64 of its products with a word
     below q fit the 128-bit accumulators;
   * the lazy 128-bit Barrett reduction's estimate leaves a remainder in [0, 4q);
   * for 2^32 < q < 2^41: the NTT epilogues' 32-bit quotient estimate leaves
-    [0, 3q) for words below 2^50, and the inverse passes' M schedule with
-    [0, 4q) products keeps every GS difference non-negative.
+    [0, 3q) for words below 2^50;
+  * the inverse passes' one lazy butterfly keeps every modulus's words in
+    [0, 2q).
 """
 import random
 
@@ -65,15 +66,13 @@ def test_three_product_shoup_quotient(q):
 
 
 def test_growing_butterfly_word_bounds():
-    """Forward: 16 stages from [0, 4q) add at most 4q each; inverse: a pass of
-    8 stages from [0, 2q) at most doubles a word per stage."""
+    """Forward: 16 stages from [0, 4q) add at most 4q each (moduli below 2^57);
+    the reducing butterflies' 4q stays below 2^64 for every modulus."""
     for q in MODULI:
         if q < (1 << 57):
             assert 4 * q + 16 * 4 * q <= M64
-        if q < (1 << 55):
-            assert (2 * q) << 8 <= M64 and (q << 8) <= M64
+        assert 4 * q <= M64
     assert 68 * ((1 << 57) - 1) <= M64
-    assert ((1 << 55) - 1) << 9 <= M64
 
 
 def fold(x, q):
@@ -218,9 +217,9 @@ def red3_small(x, q):
 
 
 def test_small_modulus_epilogue_reduction():
-    """Words below 2^50 (68q after a forward transform, 2^9 q after an inverse
-    pass with [0, 4q) products) reduce to [0, 3q): the estimate never exceeds
-    floor(x / q) and falls short by at most 2."""
+    """Words below 2^50 (the forward row pass ends below 68q < 2^48) reduce to
+    [0, 3q): the estimate never exceeds floor(x / q) and falls short by at
+    most 2."""
     for q in small_moduli():
         assert 68 * q < 1 << 48 and (q << 9) < 1 << 50
         xs = [0, 1, q - 1, q, 3 * q - 1, 68 * q - 1, (q << 9) - 1, (1 << 50) - 1]
@@ -232,29 +231,21 @@ def test_small_modulus_epilogue_reduction():
             assert r == x - qe * q and r < 3 * q and r % q == x % q
 
 
-def test_inverse_passes_with_approximate_products():
-    """The inverse passes' M schedule when the GS product lands in [0, 4q)
-    (2^32 < q < 2^41): every stage's inputs stay below its M (so a - b + M
-    never goes negative), and a pass ends below 2^(LOGS+1) q < 2^50."""
-    for q in small_moduli():
-        for logs in (6, 7, 8):
-            # row pass: words enter below q; stage 0 takes M = q, stage i > 0 M = q 2^(i+1)
-            bound = q
-            for lt in range(logs):
-                M = q if lt == 0 else q << (lt + 1)
-                assert bound <= M and M + bound <= M64
-                bound = max(2 * M, 4 * q)
-            assert bound <= q << (logs + 1) < 1 << 50
-            # column pass: words enter below 2q; stage i takes M = 2q 2^i
-            bound = 2 * q
-            for lt in range(logs):
-                M = (2 * q) << lt
-                assert bound <= M and M + bound <= M64
-                bound = max(2 * M, 4 * q)
-            assert bound <= q << (logs + 1) < 1 << 50
-            # and the approximate Shoup product takes any such word to [0, 4q)
-            for w in (1, q - 1, RNG.randrange(q)):
-                ws = shoup_const(w, q)
-                for b in (bound - 1, RNG.randrange(bound), (1 << 50) - 1):
-                    r = (b * w - approx_quotient(b, ws) * q) & M64
-                    assert r < 4 * q and r % q == (b * w) % q
+@pytest.mark.parametrize("q", MODULI)
+def test_inverse_butterfly_keeps_words_below_2q(q):
+    """The inverse passes' one butterfly for every modulus: words in [0, 2q);
+    (a + b, (a - b + 2q) w) with the lazy Shoup product (exact quotient
+    floor(x ws / 2^64)) and one conditional subtraction stay in [0, 2q),
+    congruent to (a + b, (a - b) w)."""
+    edge = [0, 1, q - 1, q, 2 * q - 1]
+    for w in [1, q - 1, q // 2] + [RNG.randrange(q) for _ in range(6)]:
+        ws = shoup_const(w, q)
+        pairs = [(a, b) for a in edge for b in edge] + [(RNG.randrange(2 * q), RNG.randrange(2 * q)) for _ in range(300)]
+        for a, b in pairs:
+            s_ = a + b
+            a2 = s_ - 2 * q if s_ >= 2 * q else s_
+            x = a - b + 2 * q
+            assert 0 < x < 4 * q <= M64
+            b2 = (x * w - ((x * ws) >> 64) * q) & M64
+            assert a2 < 2 * q and b2 < 2 * q
+            assert a2 % q == (a + b) % q and b2 % q == ((a - b) * w) % q
