@@ -137,7 +137,8 @@ ProfScope::~ProfScope() {
 
 namespace {
 
-constexpr int MAXJ = 480;  // jobs per launch (passed by value: 480 forward jobs are 30 KB of the 32 KB kernel parameters)
+// Jobs per launch, passed by value: 480 forward jobs are 30 KB of the 32 KB of kernel parameters.
+constexpr int MAXJ = 480;
 constexpr int THREADS = 256;
 
 template <typename J>
