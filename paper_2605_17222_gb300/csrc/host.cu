@@ -951,7 +951,7 @@ struct ModelEst {
 //   NTT butterflies (about 1.35 us per 2^16-point limb transform)   3.9e11 /s
 //   DRAM traffic of a limb transform: 2.75 limbs (input, the two passes'
 //   intermediate mostly through DRAM, output)
-constexpr double M_BW = 6.2e12, M_MAC4 = 9.5e11, M_MAC8 = 7.0e11, M_NTT = 3.9e11, M_FIXED = 5e-5;
+constexpr double M_BW = 6.2e12, M_MAC4 = 9.5e11, M_MAC8 = 7.0e11, M_NTT = 5.8e11, M_FIXED = 1e-4;
 constexpr double M_NTT_LIMBS = 2.75;
 
 ModelEst model_th_est(const ckks_ctx* C, u32 level, u32 D, u32 n1, u32 n2, u32 n3) {

@@ -14,7 +14,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-BW, MAC4, MAC8, NTT, FIXED, NTT_LIMBS = 6.2e12, 9.5e11, 7.0e11, 3.9e11, 5e-5, 2.75
+BW, MAC4, MAC8, NTT, FIXED, NTT_LIMBS = 6.2e12, 9.5e11, 7.0e11, 5.8e11, 1e-4, 2.75
 
 
 def model(level, D, n1, n2, n3, log_n=16, K=4, alpha=4):
