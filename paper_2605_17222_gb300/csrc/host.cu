@@ -135,6 +135,7 @@ struct ckks_ctx {
     u32 log_n = 0, N = 0, L = 0, K = 0, dnum = 0, alpha = 0, beta_max = 0;
     std::vector<u64> mods;  // q_0..q_{L-1}, p_0..p_{K-1}
     DevBuf d_mods, d_psi, d_ipsi, d_lift, d_lift_sh, d_err;
+    std::vector<u64> lift_c, lift_sh;  // host copies: [P]_{q_t} and its Shoup companion per Q limb
     NttTables T{};
     std::map<u32, LevelConsts> levels;
     std::map<u32, u64*> keys;  // rotation (mod N/2) -> [beta_max][L+K][N] word pairs (components interleaved)
@@ -354,8 +355,10 @@ void release_lanes(ckks_ctx* C, cudaStream_t st) {
 // (gathered through x -> x^gal if gal) -> digits_i [beta][level+K][N].
 // Y: scratch [count][level][N].  One launch pair per transform direction
 // covers every polynomial, so small steps still fill the GPU.
+// extra: further elementwise jobs (FWD_COPY) to run in the forward launch.
 void op_decompose_batch(ckks_ctx* C, u32 level, const std::vector<const u64*>& cs, u32 gal,
-                        const std::vector<u64*>& digits, u64* Y, cudaStream_t st) {
+                        const std::vector<u64*>& digits, u64* Y, cudaStream_t st,
+                        const std::vector<FwdJob>* extra = nullptr) {
     const LevelConsts& LC = C->lc(level);
     const u32 N = C->N, ext = level + C->K, beta = C->beta(level);
     const u32 cnt = (u32)cs.size();
@@ -392,11 +395,13 @@ void op_decompose_batch(ckks_ctx* C, u32 level, const std::vector<const u64*>& c
                                     nullptr, gal, 0, j, FWD_COPY});
         }
     }
+    if (extra) fj.insert(fj.end(), extra->begin(), extra->end());
     launch_fwd_ntt(C->T, fj.data(), (int)fj.size(), st);
 }
 
-void op_decompose(ckks_ctx* C, u32 level, const u64* c, u32 gal, u64* digits, u64* Y, cudaStream_t st) {
-    op_decompose_batch(C, level, std::vector<const u64*>{c}, gal, std::vector<u64*>{digits}, Y, st);
+void op_decompose(ckks_ctx* C, u32 level, const u64* c, u32 gal, u64* digits, u64* Y, cudaStream_t st,
+                  const std::vector<FwdJob>* extra = nullptr) {
+    op_decompose_batch(C, level, std::vector<const u64*>{c}, gal, std::vector<u64*>{digits}, Y, st, extra);
 }
 
 // Modulus switch down of `count` polynomials over a contiguous source run:
@@ -569,7 +574,14 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
     u64* Y = ar.limbs(std::max<size_t>((size_t)nb * level, 2 * (C->K + 1)));
     std::vector<u64*> A(n1, nullptr), B(n1, nullptr), Dg(n1, nullptr);
     Dg[0] = ar.limbs((size_t)beta * ext);
-    op_decompose(C, level, io.c1, 0, Dg[0], Y, st);  // line 1
+    // P c0 once (line 2), read by every middle-layer step of the first baby index: scaling jobs
+    // of the line-1 Decompose's forward launch
+    u64* c0l = ar.limbs(level);
+    std::vector<FwdJob> lift_jobs;
+    for (u32 t = 0; t < level; t++)
+        lift_jobs.push_back(FwdJob{io.c0 + (size_t)t * N, c0l + (size_t)t * N, nullptr, nullptr, nullptr,
+                                   C->lift_c[t], C->lift_sh[t], t, FWD_COPY | FWD_SCALE});
+    op_decompose(C, level, io.c1, 0, Dg[0], Y, st, &lift_jobs);  // line 1
     for (u32 i = 1; i < n1; i++) {                     // lines 2-5 (the lift is fused)
         const int64_t r = s * i;
         A[i] = ar.limbs(ext);
@@ -598,11 +610,7 @@ void sched_th(ckks_ctx* C, u32 level, LtIO io, const ckks_diags* f, u32 n1, u32 
     a.B[0] = io.c1;
     a.c0[0] = io.c0;
     a.c1[0] = io.c1;
-    {  // P c0 once (line 2), read by every middle-layer step of the first baby index
-        u64* c0l = ar.limbs(level);
-        launch_lift((const ModC*)C->d_mods.p, C->d_lift.p, C->d_lift_sh.p, &io.c0, &c0l, 1, level, C->log_n, st);
-        a.c0l[0] = c0l;
-    }
+    a.c0l[0] = c0l;
     for (u32 i = 1; i < n1; i++) a.A[i] = A[i], a.B[i] = B[i];
     for (u32 i = 0; i < n1; i++) a.Dg[i] = Dg[i];
     for (u32 j = 1; j < n2; j++) {
@@ -1215,6 +1223,8 @@ ckks_status ckks_ctx_create(ckks_ctx** out, uint32_t log_n, const uint64_t* q, u
         CK(cudaMemset(C->d_err.p, 0, 8));
         C->d_lift.p = C->upload(lift);
         C->d_lift_sh.p = C->upload(lsh);
+        C->lift_c = lift;
+        C->lift_sh = lsh;
         C->T = NttTables{(const ModC*)C->d_mods.p, (const ulonglong2*)C->d_psi.p, (const ulonglong2*)C->d_ipsi.p,
                          log_n};
         *out = C.release();

@@ -27,7 +27,10 @@ struct NttTables {
 // FwdJob::nsrc bit 17: a copy job, dst[x] = src[x -> x^gal] with gal in c
 // (0: plain copy) and no transform, for the limbs a Decompose passes through
 // unchanged; it rides in the same launch as the transforms.
+// Bit 18 (with bit 17): a scaling job instead, dst[x] = src[x] * c mod q
+// (c_sh its Shoup companion), e.g. the lift P c0 of Alg. 2 line 2.
 constexpr u32 FWD_COPY = 1u << 17;
+constexpr u32 FWD_SCALE = 1u << 18;
 struct FwdJob {
     const u64* src;
     u64* dst;

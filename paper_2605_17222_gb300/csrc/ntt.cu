@@ -371,12 +371,17 @@ __global__ void __launch_bounds__(THREADS, 4) k_fwd_cols(const __grid_constant__
     const u64 q = m.q;
     const ulonglong2* tw = T.psi + (size_t)J.mod * N;
     if (J.nsrc & FWD_COPY) {  // a pass-through limb: the block copies its columns (every word loaded first)
-        const u32 gal = (u32)J.c;
         u64 y[16];
+        if (J.nsrc & FWD_SCALE) {
 #pragma unroll
-        for (int v = 0; v < 16; v++) {
-            const u32 idx = (u + TPL * v) * C + col;
-            y[v] = J.src[gal ? auto_src(idx, gal, LOGN) : idx];
+            for (int v = 0; v < 16; v++) y[v] = mul_shoup(J.src[(u + TPL * v) * C + col], J.c, J.c_sh, q);
+        } else {
+            const u32 gal = (u32)J.c;
+#pragma unroll
+            for (int v = 0; v < 16; v++) {
+                const u32 idx = (u + TPL * v) * C + col;
+                y[v] = J.src[gal ? auto_src(idx, gal, LOGN) : idx];
+            }
         }
 #pragma unroll
         for (int v = 0; v < 16; v++) J.dst[(size_t)(u + TPL * v) * C + col] = y[v];
