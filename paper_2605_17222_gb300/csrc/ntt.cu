@@ -137,8 +137,10 @@ ProfScope::~ProfScope() {
 
 namespace {
 
-// Jobs per launch, passed by value: 480 forward jobs are 30 KB of the 32 KB of kernel parameters.
-constexpr int MAXJ = 480;
+// Jobs per launch, passed by value: 510 forward jobs (64 bytes each) and the tables fill the
+// 32,764 bytes of kernel parameters; a level-24 Decompose of three polynomials (504 jobs) is one launch.
+constexpr int MAXJ = 510;
+static_assert(sizeof(FwdJob) * MAXJ + sizeof(NttTables) <= 32764, "forward jobs exceed the kernel parameter space");
 constexpr int THREADS = 256;
 
 template <typename J>
