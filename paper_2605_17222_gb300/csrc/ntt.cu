@@ -141,6 +141,8 @@ namespace {
 // 32,764 bytes of kernel parameters; a level-24 Decompose of three polynomials (504 jobs) is one launch.
 constexpr int MAXJ = 510;
 static_assert(sizeof(FwdJob) * MAXJ + sizeof(NttTables) <= 32764, "forward jobs exceed the kernel parameter space");
+static_assert(sizeof(InvJob) * MAXJ + sizeof(NttTables) <= 32764, "inverse jobs exceed the kernel parameter space");
+static_assert(sizeof(AddJob) * MAXJ + 64 <= 32764, "add jobs exceed the kernel parameter space");
 constexpr int THREADS = 256;
 
 template <typename J>
